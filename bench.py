@@ -1,0 +1,354 @@
+"""Benchmark: superiorized iterations/s on the clinical-size synthetic plan.
+
+Workload: 200 x 200 x 150 water phantom at 2 mm (6e6 voxels), three coplanar
+fields at 0/90/270 degrees, 30000 spots, D and L in FP32 CSR with one shared
+pattern (5.6e8 nonzeros each), PTV ellipsoid 150 cc and three OARs with dose
+and LETd limits; w0 = 1, alpha 0.99, relaxation 1.  One step = one
+superiorized iteration (Fig. 3 around the simultaneous Fig. 2): two fused
+forward products and two transposed products over every voxel row.
+
+Output: one JSON line (rank 0).  `value` is device throughput with the plan
+resident in HBM; `e2e` is one full plan re-optimisation (500 iterations)
+through the public C ABI from pinned host buffers; `roofline` is the dominant
+kernel's algorithmic bytes / its CUDA-event time on the library stream;
+`cpu_baseline` is the FP64 oracle on a bounded sample (one iteration of the
+same plan) on the host cores.  `--impl reference` times that oracle as the
+reference arm.  With --gpus N each rank runs an independent replica (the
+path has no exchange step): value = all ranks' iterations / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "superiorized iters/s & SpMV %HBM peak; serving plans/hr, p99 latency vs plain FP32"
+UNIT = "iters/s"
+WORKLOAD = ("clinical: 200x200x150 voxels at 2 mm, 3 fields 0/90/270 deg, 30000 spots, "
+            "FP32 CSR D and L (shared pattern), PTV 150 cc + 3 OARs, w0=1, alpha 0.99, relaxation 1")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def fwd_bytes(nnz, rows, vb, n_launch_obj, n_launch_bc):
+    """Algorithmic bytes of the forward launches: the shared index stream
+    (4 B) and both value streams (vb B each) per nonzero, row_ptr (8 B) and
+    the (Dx, Lx) pair (8 B) per row; OBJ adds mask (4) + residual (8) per row,
+    BC adds mask (4) + residual read (8) per row."""
+    base = nnz * (4 + 2 * vb) + rows * (8 + 8)
+    return (n_launch_obj + n_launch_bc) * (base + rows * 12)
+
+
+def bwd_bytes(nnz, n_hot, n_chunks, vb, n_grad, n_proj):
+    """Transposed launches: row index (4 B) + L (vb) [+ D (vb) for the
+    projection pass, and for a gradient with DOSE terms] per nonzero, the
+    coefficient pair read once (8 B per row), chunk pointer (8 B) and chunk
+    sum (4 B) per chunk."""
+    g = nnz * (4 + vb) + n_hot * 8 + n_chunks * 12
+    p = nnz * (4 + 2 * vb) + n_hot * 8 + n_chunks * 12
+    return n_grad * g + n_proj * p
+
+
+SMALL = dict(shape=(100, 100, 75), h=4.0)  # same phantom at half resolution (profiling case)
+
+
+def make_plan(seed, small=False):
+    import phantom
+    return phantom.clinical_plan(seed=seed, **(SMALL if small else {}))
+
+
+def run_gpu_arm(args):
+    import torch
+    import phantom
+    from paper_2509_20012_gb300 import Handle, default_params
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    t_gen = time.perf_counter()
+    plan = make_plan(seed=args.seed + rank, small=args.small)
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.Stream(device=local)
+    hbm, hbm_src = peaks()
+    out = {}
+
+    def timed_run(rows, fmt="fp32"):
+        h = Handle(local, stream=stream)
+        t0 = time.perf_counter()
+        h.load_plan(plan, fmt=fmt, rows=rows)
+        t_load = time.perf_counter() - t0
+        sz = h.sizes()
+        # plain launches with CUDA events around every kernel on the library stream
+        h.set_timing(True)
+        h.begin(plan.w0, plan.alpha, plan.relaxation)
+        h.iterate(args.warmup)
+        torch.cuda.synchronize()
+        h.set_timing(True)  # reset the counters: only the timed region below counts
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.iterate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        kt = h.get_timing()
+        launches = h.launch_count()
+        w, dose, letd, rep = h.end()
+        h.close()
+        vb = 4 if fmt == "fp32" else 2
+        nf = kt["forward"][1]
+        nb = kt["backward"][1]
+        n_iter = args.steps
+        fb = fwd_bytes(sz["nnz_rows"], sz["n_rows"], vb, n_iter, n_iter)
+        # chunk count is internal; it is small next to nnz (bounded by nnz/256 + n_spots)
+        n_chunks_est = sz["nnz_rows"] // 2048 + sz["n_spots"]
+        bb = bwd_bytes(sz["nnz_rows"], sz["n_rows"], n_chunks_est, vb, n_iter, n_iter)
+        f_ms, b_ms = kt["forward"][0], kt["backward"][0]
+        fw = {"bound": "hbm", "achieved": fb / (f_ms * 1e-3) / 1e9 if f_ms else None, "peak": hbm,
+              "unit": "GB/s", "kernel": "k_forward (fused Dx/Lx)", "launches": nf, "ms_total": f_ms,
+              "bytes_per_launch": fb / max(1, 2 * n_iter)}
+        bw = {"bound": "hbm", "achieved": bb / (b_ms * 1e-3) / 1e9 if b_ms else None, "peak": hbm,
+              "unit": "GB/s", "kernel": "k_backward (CSC chunks)", "launches": nb, "ms_total": b_ms,
+              "bytes_per_launch": bb / max(1, 2 * n_iter)}
+        for r in (fw, bw):
+            r["frac"] = r["achieved"] / hbm if r["achieved"] else None
+        return dict(ms=ms, kt=kt, launches=launches, clocks=clocks, rep=rep, sizes=sz, t_load=t_load,
+                    fwd=fw, bwd=bw, w=w)
+
+    main = timed_run("all")
+    roi = timed_run("roi") if args.roi else None
+
+    # end to end: one plan re-optimisation from pinned host buffers through the C ABI
+    e2e = None
+    if args.e2e_iters > 0:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(plan, k))).pin_memory()
+               for k in ("row_ptr", "col", "D", "L")}
+        pin_mask = torch.from_numpy(plan.mask.view(np.int32)).pin_memory()
+        pin_w0 = torch.from_numpy(plan.w0).pin_memory()
+        out_w = torch.empty(plan.n_spots, dtype=torch.float32).pin_memory()
+        out_d = torch.empty(plan.n_vox, dtype=torch.float32).pin_memory()
+        out_l = torch.empty(plan.n_vox, dtype=torch.float32).pin_memory()
+        h = Handle(local, stream=stream)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.load_influence(pin["row_ptr"], pin["col"], pin["D"], pin["L"], pin_mask, plan.n_spots)
+        h.set_constraints(plan.constraints)
+        h.set_objective(plan.objective)
+        h.superiorize(pin_w0, args.e2e_iters, plan.alpha, plan.relaxation, outputs=(out_w, out_d, out_l))
+        t_e2e = time.perf_counter() - t0
+        h.close()
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([t_e2e], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = sum(v.numel() * v.element_size() for v in pin.values()) + pin_mask.numel() * 4 + plan.n_spots * 4
+        d2h = (plan.n_spots + 2 * plan.n_vox) * 4
+        e2e = {"value": ws * args.e2e_iters / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.e2e_iters, "d2h_bytes_per_step": d2h / args.e2e_iters,
+               "what": f"load_influence from pinned host + set_constraints + set_objective + "
+                       f"superiorize({args.e2e_iters} iters) with host w0/w/dose/LETd; {t_e2e:.3f} s"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_iters > 0:
+        cpu = cpu_baseline(plan, args.cpu_iters)
+
+    if rank == 0:
+        dom = main["fwd"] if (main["fwd"]["ms_total"] or 0) >= (main["bwd"]["ms_total"] or 0) else main["bwd"]
+        value = ws * args.steps / (main["ms"] * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": "all voxel rows streamed every pass",
+                       "n_vox": main["sizes"]["n_vox"], "n_spots": main["sizes"]["n_spots"],
+                       "nnz_per_matrix": main["sizes"]["nnz"], "storage": "fp32",
+                       "l2": "inputs larger than L2 (each pass streams %.1f GB)" % (
+                           main["sizes"]["nnz"] * 12 / 1e9),
+                       "parallelism": f"replicas{ws}", "generate_s": round(t_gen, 2),
+                       "load_s": round(main["t_load"], 3)},
+            "roofline": {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac")} | {
+                "traffic": None, "kernel": dom["kernel"], "peak_source": hbm_src,
+                "forward": main["fwd"], "backward": main["bwd"]},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": main["launches"],
+            "clocks": main["clocks"],
+            "kernel_ms": {k: v[0] for k, v in main["kt"].items()},
+            "final": {"objective": main["rep"]["objective"], "n_violated": main["rep"]["n_violated"],
+                      "max_violation": main["rep"]["max_violation"]},
+        }
+        if roi is not None:
+            line["roi_rows"] = {"value": ws * args.steps / (roi["ms"] * 1e-3),
+                                "ms_per_step": roi["ms"] / args.steps,
+                                "n_rows": roi["sizes"]["n_rows"], "nnz_rows": roi["sizes"]["nnz_rows"],
+                                "forward": roi["fwd"], "backward": roi["bwd"], "clocks": roi["clocks"],
+                                "max_abs_w_diff_vs_all_rows": float(np.max(np.abs(roi["w"] - main["w"])))}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(plan, iters):
+    """FP64 oracle, as it stands, on `iters` iterations of the same plan."""
+    import oracle
+    P = oracle.build_problem(plan.row_ptr, plan.col, plan.D, plan.L, plan.n_spots, plan.mask,
+                             plan.constraints, plan.objective)
+    R = oracle.constraint_rows(P)
+    t0 = time.perf_counter()
+    oracle.superiorize(P, plan.w0, iters, plan.alpha, plan.relaxation, rows=R)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} superiorized iteration(s) of the clinical plan (FP64 numpy/scipy, "
+                      f"single-threaded sparse products), {dt:.1f} s; setup excluded"}
+
+
+def run_reference_arm(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    plan = make_plan(seed=args.seed, small=args.small)
+    P = oracle.build_problem(plan.row_ptr, plan.col, plan.D, plan.L, plan.n_spots, plan.mask,
+                             plan.constraints, plan.objective)
+    R = oracle.constraint_rows(P)
+    w = plan.w0.astype(np.float64)
+    s = 0
+    beta0 = 0.1 * float(np.linalg.norm(w))
+    k = 0
+    for _ in range(args.ref_warmup):
+        w, log = oracle.superiorize(P, w, 1, plan.alpha, plan.relaxation, rows=R, beta0=beta0, s0=s, k0=k)
+        s, k = log[-1]["s"], k + 1
+    t0 = time.perf_counter()
+    for _ in range(args.ref_steps):
+        w, log = oracle.superiorize(P, w, 1, plan.alpha, plan.relaxation, rows=R, beta0=beta0, s0=s, k0=k)
+        s, k = log[-1]["s"], k + 1
+    dt = time.perf_counter() - t0
+    v = args.ref_steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.ref_steps, "warmup": args.ref_warmup, "ms_per_step": dt * 1e3 / args.ref_steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "rows": "all voxel rows"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.ref_steps} timed iteration(s) after {args.ref_warmup} "
+                                       f"warm-up, FP64 oracle, single-threaded sparse products"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-roi", dest="roi", action="store_false")
+    ap.add_argument("--e2e-iters", type=int, default=500)
+    ap.add_argument("--cpu-iters", type=int, default=1)
+    ap.add_argument("--small", action="store_true",
+                    help="half-resolution phantom (100x100x75 at 4 mm) for profiler captures")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    # the reference arm (FP64 oracle on the host cores) is bounded: one
+    # iteration of the clinical plan takes ~10-20 s
+    args.ref_steps = max(1, min(args.steps, 2))
+    args.ref_warmup = 0
+    if args.impl == "reference":
+        run_reference_arm(args)
+    else:
+        run_gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,262 @@
+/*
+ * fredopt.h - C ABI of the GB300 (sm_103a) implementation of simultaneous
+ * dose and LETd proton plan optimisation by superiorized feasibility seeking
+ * (arXiv 2509.20012: Sec. 2.4.3, Fig. 2, Fig. 3, Eq. 2).
+ *
+ * One handle holds one plan: the dose-influence matrix D (Gy per unit spot
+ * weight) and the LET-weighted matrix L (Gy*keV/um; L_ij = LET_ij * D_ij,
+ * the additive numerator of Eq. 1 per pencil beam, Sec. 2.2) with one shared
+ * CSR sparsity pattern, the voxel -> structure bitmask, the constraint table
+ * and the objective.  Everything after fredopt_load_influence is resident on
+ * the device; an iteration makes no host round trip.
+ *
+ * Conventions for every call:
+ *   - Return 0 (FREDOPT_OK) or a negative FREDOPT_ERR_* code; nothing throws
+ *     across the ABI.  The handle stays usable after an error.
+ *     fredopt_last_error() gives a message for the last failing call on the
+ *     handle.
+ *   - Pointer arguments are caller-owned.  Unless FREDOPT_DEVICE_PTR is set
+ *     in `flags`, they are host pointers (pageable or pinned); with it, they
+ *     are device pointers on the handle's device.  Inputs are consumed before
+ *     the call returns; outputs are complete when it returns (the library
+ *     synchronises its stream at the end of every call that returns data).
+ *   - Voxel arrays are indexed by voxel (row of D and L), spot arrays by spot
+ *     (column).  Floating point values are IEEE binary32 unless noted.
+ *   - A handle is not thread-safe; distinct handles may be used from
+ *     distinct threads.
+ */
+#ifndef FREDOPT_H
+#define FREDOPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FREDOPT_OK 0
+#define FREDOPT_ERR_INVALID_ARG (-1) /* bad scalar argument or null pointer */
+#define FREDOPT_ERR_SHAPE (-2)       /* sizes inconsistent or out of range */
+#define FREDOPT_ERR_PATTERN (-3)     /* CSR not monotone, column out of range or unsorted */
+#define FREDOPT_ERR_NONFINITE (-4)   /* NaN or Inf in an input */
+#define FREDOPT_ERR_NOT_LOADED (-5)  /* call needs a loaded plan / constraints / begun solve */
+#define FREDOPT_ERR_OOM (-6)         /* device allocation failed */
+#define FREDOPT_ERR_CUDA (-7)        /* CUDA runtime error (message via fredopt_last_error) */
+#define FREDOPT_ERR_TIMEOUT (-8)     /* a bounded device-side wait gave up */
+#define FREDOPT_ERR_UNSUPPORTED (-9) /* option not available in this build */
+
+/* ---- flags ---- */
+#define FREDOPT_DEVICE_PTR 0x1u /* pointer args are device pointers */
+
+/* value storage formats of fredopt_load_influence (low byte of `format`) */
+#define FREDOPT_FP32 0 /* D, L stored as float */
+#define FREDOPT_BF16 1 /* bfloat16 with one float scale per row and matrix */
+#define FREDOPT_FP16 2 /* binary16 with one float scale per row and matrix */
+/* row set of the iteration (or'ed into `format`) */
+#define FREDOPT_ROWS_ALL 0x000 /* every voxel row is streamed every pass (default) */
+#define FREDOPT_ROWS_ROI 0x100 /* only rows of voxels in some structure are streamed;
+                                  dose/LETd of the other voxels are computed at the end */
+
+/* ---- constraint kinds (Fig. 2 half-spaces; LETd limit as in the benchmark spec) ----
+ * DOSE_MAX / DOSE_MIN : (D w)_i <= / >= bound                        (Gy)
+ * CDL_MAX  / CDL_MIN  : c (L w)_i <= / >= bound, c = params.c_cdl    (Gy)
+ * LETD_MAX / LETD_MIN : ((L - bound D) w)_i <= / >= 0, i.e. LETd_i <= / >= bound (keV/um)
+ */
+#define FREDOPT_DOSE_MIN 0
+#define FREDOPT_DOSE_MAX 1
+#define FREDOPT_CDL_MIN 2
+#define FREDOPT_CDL_MAX 3
+#define FREDOPT_LETD_MIN 4
+#define FREDOPT_LETD_MAX 5
+
+typedef struct fredopt_constraint {
+  uint32_t struct_bit; /* 0..31: the structure whose voxels carry this constraint */
+  int32_t kind;        /* FREDOPT_DOSE_MIN .. FREDOPT_LETD_MAX */
+  double bound;        /* Gy (dose, cDL) or keV/um (LETd) */
+  double priority;     /* structure weight p_S > 0 (Fig. 2 "w_i"; Sec. 2.4.3) */
+} fredopt_constraint;
+
+/* objective quantities of Eq. 2: q_i = (D w)_i or c (L w)_i */
+#define FREDOPT_Q_DOSE 0
+#define FREDOPT_Q_CDL 1
+
+typedef struct fredopt_objective_term {
+  uint32_t struct_bit; /* structure whose voxels enter this term */
+  int32_t quantity;    /* FREDOPT_Q_DOSE or FREDOPT_Q_CDL */
+  double target;       /* D-hat_i or cDL-hat_i of Eq. 2 */
+  double weight;       /* w_i of Eq. 2 (> 0) */
+} fredopt_objective_term;
+
+/* Cimmino weight normalisation */
+#define FREDOPT_NORM_ALL 0      /* omega_r = p_r / sum of p over all reachable rows */
+#define FREDOPT_NORM_VIOLATED 1 /* omega_r = p_r / sum of p over rows violated now */
+
+typedef struct fredopt_params {
+  double beta0;           /* first trial step; < 0 selects 0.1 * ||w0||_2 (default -1) */
+  double eta;             /* priority decay per iteration, 0 < eta <= 1 (default 1) */
+  int32_t reductions;     /* perturbation steps per iteration, N >= 0 (default 1; 0 = plain
+                             feasibility seeking, Fig. 2 alone) */
+  int32_t max_trials;     /* cap of the trial loop per step, >= 1 (default 50) */
+  int32_t cimmino_norm;   /* FREDOPT_NORM_* (default FREDOPT_NORM_ALL) */
+  int32_t grad_normalize; /* 1: unit direction -g/||g|| (default); 0: raw -g (Fig. 3 literal) */
+  double c_cdl;           /* c of cDL = c * dose * LETd, um/keV (default 0.04, Sec. 2.4) */
+  int32_t log_capacity;   /* per-iteration log entries kept on the device (default 4096) */
+  int32_t use_graphs;     /* 1: replay iterations as CUDA graphs (default); 0: plain launches */
+} fredopt_params;
+
+typedef struct fredopt_log_entry {
+  int64_t k;           /* iteration index */
+  int64_t s;           /* global trial counter after this iteration's perturbation phase */
+  int32_t accepted;    /* accepted perturbation steps this iteration */
+  int32_t n_violated;  /* constraint rows violated at the point the feasibility step saw */
+  double beta;         /* last accepted step (0 if none) */
+  double f_start;      /* objective at w^k */
+  double f_end;        /* objective at the perturbed point (closed form on the device) */
+  double gnorm;        /* ||grad f|| of the last perturbation step */
+  double max_violation;/* largest violation (bound units) at that point */
+} fredopt_log_entry;
+
+typedef struct fredopt_report {
+  int64_t iters;               /* iterations run since fredopt_begin */
+  int64_t s;                   /* trial counter */
+  int64_t accepted;            /* accepted perturbation steps in total */
+  int64_t n_rows;              /* reachable constraint rows */
+  int64_t unreachable_rows;    /* rows skipped because |a_r|^2 == 0 */
+  int64_t n_violated;          /* rows violated at the final w (FP64 check) */
+  double objective;            /* f(w) at the final w, FP64 */
+  double max_violation[6];     /* per kind (index = FREDOPT_* kind), FP64, bound units */
+  double beta0;                /* step actually used */
+  double device_ms;            /* device time of fredopt_iterate calls since fredopt_begin */
+} fredopt_report;
+
+typedef struct fredopt_ctx* fredopt_t;
+
+/* Fill `p` with the defaults listed above. */
+void fredopt_default_params(fredopt_params* p);
+
+/* Human-readable name of a status code (static storage). */
+const char* fredopt_strerror(int code);
+
+/* Message of the last failing call on `h` (valid until the next call on h). */
+const char* fredopt_last_error(fredopt_t h);
+
+/* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * on that device that all work of the handle is ordered on, or NULL for a
+ * stream owned by the handle.  The caller keeps ownership of its stream. */
+int fredopt_create(fredopt_t* out, int device, void* cuda_stream);
+
+/* Free every device resource of the handle. */
+int fredopt_destroy(fredopt_t h);
+
+/* Load the influence-matrix pair (Sec. 2.2; the stage-(iii) upload of
+ * Table 2).  row_ptr int64[n_vox+1] with row_ptr[0] = 0 and row_ptr[n_vox] =
+ * nnz; col int32[nnz] strictly increasing within a row, 0 <= col < n_spots;
+ * D_val, L_val float[nnz] finite; voxel_mask uint32[n_vox] (bit b: voxel in
+ * structure b).  `format` = FREDOPT_FP32|BF16|FP16 | FREDOPT_ROWS_ALL|ROI.
+ * The data is validated on the device (FREDOPT_ERR_PATTERN / NONFINITE),
+ * the CSC copy of the streamed rows is built (values moved bit-exactly), the
+ * values are quantised if asked, and the FP64 row moments |D_i|^2, |L_i|^2,
+ * <D_i, L_i> are computed from the stored values.  Replaces any loaded plan
+ * and clears constraints, objective and solve state. */
+int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t nnz,
+                           const int64_t* row_ptr, const int32_t* col, const float* D_val,
+                           const float* L_val, const uint32_t* voxel_mask, int format,
+                           uint32_t flags);
+
+/* Constraint table (Fig. 2; priorities as in Sec. 2.4.3).  Copies `c`.
+ * bound must be finite, priority > 0, struct_bit < 32.  Rows whose
+ * |a_r|^2 is zero are unreachable and skipped. */
+int fredopt_set_constraints(fredopt_t h, int n, const fredopt_constraint* c);
+
+/* Objective terms (Eq. 2).  n = 0 sets no objective (plain feasibility). */
+int fredopt_set_objective(fredopt_t h, int n, const fredopt_objective_term* t);
+
+/* Start a solve at w0 (float[n_spots], >= 0): 0 < alpha < 1 (Fig. 3),
+ * 0 < relaxation <= 2 (Fig. 2), params may be NULL (defaults). */
+int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
+                  const fredopt_params* params, uint32_t flags);
+
+/* Run `iters` superiorized iterations (Fig. 3 around the simultaneous form
+ * of Fig. 2) on the device.  Asynchronous with respect to the host unless
+ * an error is detected; returns FREDOPT_ERR_TIMEOUT if a device wait gave up. */
+int fredopt_iterate(fredopt_t h, int iters);
+
+/* Finish: w_out float[n_spots]; dose_out, letd_out float[n_vox] in voxel
+ * order (LETd = Lw/Dw, 0 where Dw = 0; Eq. 1) from an FP64-accumulated final
+ * product; the FP64 feasibility and objective check goes to `rep`.  Any
+ * output pointer may be NULL. */
+int fredopt_end(fredopt_t h, float* w_out, float* dose_out, float* letd_out, fredopt_report* rep,
+                uint32_t flags);
+
+/* begin + iterate(iters) + end in one call. */
+int fredopt_superiorize(fredopt_t h, const float* w0, int iters, double alpha, double relaxation,
+                        const fredopt_params* params, float* w_out, float* dose_out,
+                        float* letd_out, fredopt_report* rep, uint32_t flags);
+
+/* Copy up to `max_entries` entries of the per-iteration log (oldest first,
+ * the most recent log_capacity iterations); returns the count (>= 0) or an
+ * error code. */
+int fredopt_get_log(fredopt_t h, fredopt_log_entry* out, int max_entries);
+
+/* Checkpoint / resume of a begun solve: w (float[n_spots]), iteration k and
+ * trial counter s.  set_state after begin continues exactly where
+ * get_state was taken (same plan, constraints and parameters). */
+int fredopt_get_state(fredopt_t h, float* w, int64_t* k, int64_t* s, uint32_t flags);
+int fredopt_set_state(fredopt_t h, const float* w, int64_t k, int64_t s, uint32_t flags);
+
+/* ---- single passes of the iteration, for tests and tools ---- */
+
+/* Dose D w and LET-weighted dose L w of every voxel (voxel order), FP32
+ * accumulation, one fused pass over the stored values. */
+int fredopt_forward(fredopt_t h, const float* w, float* dose_out, float* lw_out, uint32_t flags);
+
+/* u = D^T a_D + L^T a_L over the streamed rows (the transposed product of
+ * the projection and gradient steps).  a_D, a_L float[n_vox] in voxel order;
+ * entries of voxels outside the streamed rows are ignored. */
+int fredopt_backward(fredopt_t h, const float* a_D, const float* a_L, float* u_out, uint32_t flags);
+
+/* One simultaneous feasibility step from x (Fig. 2, simultaneous form):
+ * w_out = max(0, x + relaxation * prio_scale * sum_r omega_r t_r a_r).
+ * Needs constraints.  norm = FREDOPT_NORM_*. */
+int fredopt_feasibility_step(fredopt_t h, const float* x, double relaxation, double prio_scale,
+                             int norm, float* w_out, uint32_t flags);
+
+/* Objective f(x) (Eq. 2 terms, FP64 reduction) and its gradient g (float[n_spots]). */
+int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_out, uint32_t flags);
+
+/* ---- inspection of the device data (bit-exact copies) ---- */
+
+/* Sizes: n_vox, n_spots, nnz, number of streamed rows, nnz of the streamed rows. */
+int fredopt_get_sizes(fredopt_t h, int64_t* n_vox, int64_t* n_spots, int64_t* nnz,
+                      int64_t* n_rows, int64_t* nnz_rows);
+
+/* The streamed rows: voxel index (int64[n_rows]) and structure mask
+ * (uint32[n_rows]) in device order. Host pointers. */
+int fredopt_get_rows(fredopt_t h, int64_t* voxel, uint32_t* mask);
+
+/* The CSC copy of the streamed rows: col_ptr int64[n_spots+1], row (index
+ * into the streamed rows) int32[nnz_rows], D and L values float[nnz_rows]
+ * (dequantised: scale * stored value for BF16/FP16). Host pointers. */
+int fredopt_get_csc(fredopt_t h, int64_t* col_ptr, int32_t* row, float* D_val, float* L_val);
+
+/* FP64 row moments |D_i|^2, |L_i|^2, <D_i, L_i> of the streamed rows. */
+int fredopt_get_moments(fredopt_t h, double* dd, double* ll, double* dl);
+
+/* Device time (ms, CUDA events on the handle's stream) and launch count of
+ * each kernel class since the last reset, when timing is enabled.  Classes:
+ * 0 forward product, 1 transposed product, 2 constraint evaluation,
+ * 3 column finish, 4 scalar finish, 5 other. */
+#define FREDOPT_KCLASS_N 6
+int fredopt_set_timing(fredopt_t h, int enable);
+int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);
+
+/* Number of kernels the handle has enqueued since the last
+ * fredopt_set_timing call (a CUDA-graph replay counts each of its kernels);
+ * -1 for a null handle. */
+int64_t fredopt_launch_count(fredopt_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FREDOPT_H */

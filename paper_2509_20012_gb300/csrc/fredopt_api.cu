@@ -1,0 +1,1277 @@
+// C ABI of libfredopt (include/fredopt.h): plan upload and setup (stage
+// (iii) of Table 2), the device-resident iteration of Fig. 3 around the
+// simultaneous form of Fig. 2, and the final FP64 outputs.
+//
+// Device order of rows: with FREDOPT_ROWS_ROI the rows of voxels that belong
+// to some structure come first (ascending voxel), then all other rows; the
+// iteration streams only the first n_hot rows (Fig. 2 visits the voxels of
+// the ROIs only).  With FREDOPT_ROWS_ALL the order is the voxel order and
+// every row is streamed every pass.  The final outputs always cover every
+// voxel.
+#include "fredopt.h"
+#include "fredopt_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fo;
+
+namespace {
+
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t alloc(size_t count) {
+    release();
+    const size_t c = count ? count : 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), c * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    else p = nullptr;
+    return e;
+  }
+  cudaError_t ensure(size_t count) { return (p && n >= count) ? cudaSuccess : alloc(count); }
+};
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  int cls = 0;
+};
+
+}  // namespace
+
+struct fredopt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev_join = nullptr, ev_it0 = nullptr, ev_it1 = nullptr;
+  Geometry geo{};
+  std::string last_error;
+  size_t l2_bytes = 0;
+
+  // plan
+  bool loaded = false;
+  int fmt = 0;
+  bool roi = false;
+  int64_t V = 0, nnz = 0, n_hot = 0, nnz_hot = 0;
+  int32_t n = 0, n_pad = 0;
+  DBuf<int64_t> rp;
+  DBuf<int32_t> col;
+  DBuf<uint8_t> Dv, Lv;
+  DBuf<float> sD, sL;
+  DBuf<int64_t> voxel;  // only with ROI
+  DBuf<uint32_t> mask;  // [n_hot]
+  DBuf<double> mdd, mll, mdl;
+  DBuf<int64_t> cp;
+  DBuf<int32_t> crow;
+  DBuf<uint8_t> DTv, LTv;
+  DBuf<int64_t> warp_row_hot, warp_row_all, chunk_ptr;
+  DBuf<int32_t> col_chunk, warp_chunk;
+  int64_t n_chunks = 0;
+  bool hint_fwd = true, hint_bwd = true;
+  std::vector<int64_t> h_voxel;  // device row -> voxel (host copy)
+  std::vector<uint32_t> h_mask;  // per streamed row
+
+  // problem
+  Tables tab{};
+  bool have_con = false;
+  bool obj_dose = false;
+  double W_all = 0.0;
+  int64_t n_rows_reach = 0, n_unreach = 0;
+
+  // buffers
+  DBuf<float> w, g, xbuf, gtmp;
+  DBuf<float2> yw, yg, r, gam, yall;
+  DBuf<double2> y64;
+  DBuf<float> chunk_sum, fout_a, fout_b, vin_a, vin_b;
+  DBuf<double> part;
+  DBuf<DevState> st;
+  DBuf<LogEntry> log;
+  DBuf<int> errw;
+  size_t off_f = 0, off_bc = 0, off_g = 0, off_k2 = 0, off_fin = 0, off_cnt = 0, n_part = 0;
+
+  // solve
+  bool begun = false;
+  fredopt_params prm{};
+  double alpha = 0.99, lam = 1.0, beta0 = 0.0;
+  int64_t iters_run = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_nodes = 0;
+  double device_ms = 0.0;
+  bool it_pending = false;
+  DevState st_host{};
+
+  // timing
+  bool timing = false;
+  std::vector<Timer> timers;
+  size_t timers_used = 0;
+  double kms[FREDOPT_KCLASS_N] = {0};
+  int64_t klaunch[FREDOPT_KCLASS_N] = {0};
+  int64_t launches = 0;  // kernels enqueued (graph replays count their nodes)
+};
+
+namespace {
+
+const char* kErrNames[] = {"ok",        "invalid argument", "shape",     "pattern",
+                           "nonfinite", "not loaded",       "out of memory", "cuda error",
+                           "timeout",   "unsupported"};
+
+int fail(fredopt_t h, int code, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return code;
+}
+
+int cuda_fail(fredopt_t h, cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? FREDOPT_ERR_OOM : FREDOPT_ERR_CUDA;
+  cudaGetLastError();  // clear non-sticky errors so the handle stays usable
+  return fail(h, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool dev_ptr(uint32_t flags) { return (flags & FREDOPT_DEVICE_PTR) != 0; }
+
+// Order the handle's own stream after the legacy default stream, so device
+// inputs written there by the caller are visible.
+void join_in(fredopt_t h) {
+  if (!h->own_stream) return;
+  cudaEventRecord(h->ev_join, 0);
+  cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+}
+
+cudaError_t copy_in(fredopt_t h, void* dst, const void* src, size_t bytes, uint32_t flags) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, dev_ptr(flags) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         h->stream);
+}
+cudaError_t copy_out(fredopt_t h, void* dst, const void* src, size_t bytes, uint32_t flags) {
+  if (bytes == 0 || !dst) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, dev_ptr(flags) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         h->stream);
+}
+
+// Balanced contiguous split of rows [0, n_rows) into `parts` ranges by
+// cost(row) = nnz(row) + row_cost.  Returns parts+1 boundaries.
+std::vector<int64_t> partition_rows(const std::vector<int64_t>& rp, int64_t n_rows, int parts,
+                                    int64_t row_cost) {
+  std::vector<int64_t> b(parts + 1, n_rows);
+  b[0] = 0;
+  const double total = (double)(rp[n_rows] - rp[0]) + (double)row_cost * (double)n_rows;
+  int64_t lo = 0;
+  for (int k = 1; k < parts; ++k) {
+    const double target = total * k / parts;
+    int64_t a = lo, z = n_rows;  // first r with prefix(r) >= target
+    while (a < z) {
+      const int64_t m = (a + z) / 2;
+      const double pre = (double)(rp[m] - rp[0]) + (double)row_cost * (double)m;
+      if (pre < target) a = m + 1;
+      else z = m;
+    }
+    b[k] = a;
+    lo = a;
+  }
+  return b;
+}
+
+template <typename T>
+cudaError_t upload_vec(fredopt_t h, DBuf<T>& d, const std::vector<T>& v) {
+  cudaError_t e = d.alloc(v.size());
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream);
+}
+
+int value_bytes(int fmt) { return fmt == FREDOPT_FP32 ? 4 : 2; }
+
+void free_graph(fredopt_t h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  h->graph_nodes = 0;
+}
+
+// ---- timed launch helper ----
+template <class F>
+void run(fredopt_t h, int cls, F&& f) {
+  if (h->timing) {
+    if (h->timers_used == h->timers.size()) {
+      Timer t;
+      cudaEventCreate(&t.a);
+      cudaEventCreate(&t.b);
+      h->timers.push_back(t);
+    }
+    Timer& t = h->timers[h->timers_used++];
+    t.cls = cls;
+    cudaEventRecord(t.a, h->stream);
+    f();
+    cudaEventRecord(t.b, h->stream);
+  } else {
+    f();
+  }
+  h->launches += 1;
+}
+
+void collect_timers(fredopt_t h) {
+  if (!h->timers_used) return;
+  cudaStreamSynchronize(h->stream);
+  for (size_t i = 0; i < h->timers_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->timers[i].a, h->timers[i].b) == cudaSuccess) {
+      h->kms[h->timers[i].cls] += ms;
+      h->klaunch[h->timers[i].cls] += 1;
+    }
+  }
+  h->timers_used = 0;
+}
+
+FwdArgs fwd_args(fredopt_t h, bool hot) {
+  FwdArgs a{};
+  a.rp = h->rp.p;
+  a.col = h->col.p;
+  a.Dv = h->Dv.p;
+  a.Lv = h->Lv.p;
+  a.sD = h->fmt ? h->sD.p : nullptr;
+  a.sL = h->fmt ? h->sL.p : nullptr;
+  a.warp_row = hot ? h->warp_row_hot.p : h->warp_row_all.p;
+  a.n_x = h->n;
+  a.n_x_pad = h->n_pad;
+  a.mask = h->mask.p;
+  a.n_hot = h->n_hot;
+  a.n_warps = h->geo.fwd_warps;
+  a.st = h->st.p;
+  a.voxel = h->roi ? h->voxel.p : nullptr;
+  return a;
+}
+
+BwdArgs bwd_args(fredopt_t h, const float2* coef) {
+  BwdArgs b{};
+  b.row = h->crow.p;
+  b.Dv = h->DTv.p;
+  b.Lv = h->LTv.p;
+  b.chunk_ptr = h->chunk_ptr.p;
+  b.warp_chunk = h->warp_chunk.p;
+  b.coef = coef;
+  b.chunk_sum = h->chunk_sum.p;
+  b.n_warps = h->geo.bwd_warps;
+  return b;
+}
+
+ColArgs col_args(fredopt_t h) {
+  ColArgs c{};
+  c.col_chunk = h->col_chunk.p;
+  c.chunk_sum = h->chunk_sum.p;
+  c.n = h->n;
+  c.k2part = h->part.p + h->off_k2;
+  c.k2_blocks = h->geo.row_blocks;
+  c.W_all = h->W_all;
+  c.st = h->st.p;
+  c.log = h->log.p;
+  c.use_u = 1;
+  return c;
+}
+
+ConArgs con_args(fredopt_t h) {
+  ConArgs c{};
+  c.yw = h->yw.p;
+  c.mask = h->mask.p;
+  c.dd = h->mdd.p;
+  c.ll = h->mll.p;
+  c.dl = h->mdl.p;
+  c.sD = h->fmt ? h->sD.p : nullptr;
+  c.sL = h->fmt ? h->sL.p : nullptr;
+  c.n_hot = h->n_hot;
+  c.gam = h->gam.p;
+  c.part = h->part.p + h->off_k2;
+  c.st = h->st.p;
+  return c;
+}
+
+// One superiorized iteration (Fig. 3 around the simultaneous Fig. 2).
+void enqueue_iteration(fredopt_t h) {
+  const Geometry& G = h->geo;
+  const Tables& t = h->tab;
+  cudaStream_t s = h->stream;
+  const int N = h->prm.reductions;
+  const bool pert = N > 0 && t.n_obj > 0;
+  double* part_f = h->part.p + h->off_f;
+  double* part_bc = h->part.p + h->off_bc;
+  double* part_g = h->part.p + h->off_g;
+  FwdArgs fa = fwd_args(h, true);
+  fa.x = h->w.p;
+  fa.y = h->yw.p;
+  if (pert) {
+    fa.r_out = h->r.p;
+    fa.part = part_f;
+    run(h, 0, [&] { launch_forward(G, h->fmt, EPI_OBJ, h->hint_fwd, fa, t, s); });
+    for (int step = 0; step < N; ++step) {
+      int nf = G.fwd_warps;
+      if (step > 0) {
+        run(h, 5, [&] { launch_apply_step(h->n_hot, h->n, h->w.p, h->g.p, h->yw.p, h->yg.p, h->st.p, s); });
+        run(h, 5, [&] {
+          launch_row_objective(G, t, h->yw.p, h->mask.p, fa.sD, fa.sL, h->n_hot, h->r.p, part_f, s);
+        });
+        nf = G.row_blocks;
+      }
+      BwdArgs ba = bwd_args(h, h->r.p);
+      run(h, 1, [&] { launch_backward(G, h->fmt, h->hint_bwd, h->obj_dose, ba, s); });
+      ColArgs ca = col_args(h);
+      ca.out = h->g.p;
+      ca.part = part_g;
+      run(h, 3, [&] { launch_colfinish(G, COL_GRAD, ca, s); });
+      FwdArgs fb = fa;
+      fb.x = h->g.p;
+      fb.y = h->yg.p;
+      fb.r_in = h->r.p;
+      fb.r_out = nullptr;
+      fb.part = part_bc;
+      run(h, 0, [&] { launch_forward(G, h->fmt, EPI_BC, h->hint_fwd, fb, t, s); });
+      run(h, 4, [&] { launch_finish(step, part_f, nf, part_bc, G.fwd_warps, part_g, G.col_blocks, h->st.p, s); });
+    }
+  } else {
+    run(h, 0, [&] { launch_forward(G, h->fmt, EPI_STORE, h->hint_fwd, fa, t, s); });
+  }
+  ConArgs k2 = con_args(h);
+  k2.yg = pert ? h->yg.p : nullptr;
+  k2.use_coef = pert ? 1 : 0;
+  run(h, 2, [&] { launch_constraints(G, t, k2, s); });
+  if (t.n_con > 0) {
+    BwdArgs bb = bwd_args(h, h->gam.p);
+    run(h, 1, [&] { launch_backward(G, h->fmt, h->hint_bwd, true, bb, s); });
+  }
+  ColArgs cc = col_args(h);
+  cc.w = h->w.p;
+  cc.g = h->g.p;
+  cc.use_coef = pert ? 1 : 0;
+  cc.use_u = t.n_con > 0 ? 1 : 0;
+  cc.norm = h->prm.cimmino_norm;
+  cc.lam = h->lam;
+  cc.in_solve = 1;
+  run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
+}
+
+int need_loaded(fredopt_t h) {
+  if (!h) return FREDOPT_ERR_INVALID_ARG;
+  if (!h->loaded) return fail(h, FREDOPT_ERR_NOT_LOADED, "no influence matrices loaded");
+  return FREDOPT_OK;
+}
+
+// Upload a spot vector (n floats) into a padded device buffer.
+int load_spot_vec(fredopt_t h, DBuf<float>& dst, const float* src, uint32_t flags) {
+  CK(copy_in(h, dst.p, src, (size_t)h->n * sizeof(float), flags));
+  return FREDOPT_OK;
+}
+
+int check_sticky(fredopt_t h) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  int err = 0;
+  CK(cudaMemcpy(&err, &h->st.p->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    const int zero = 0;
+    cudaMemcpy(&h->st.p->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    return fail(h, FREDOPT_ERR_TIMEOUT, "a bounded device-side wait gave up (bulk copy)");
+  }
+  return FREDOPT_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+
+extern "C" {
+
+void fredopt_default_params(fredopt_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->beta0 = -1.0;
+  p->eta = 1.0;
+  p->reductions = 1;
+  p->max_trials = 50;
+  p->cimmino_norm = FREDOPT_NORM_ALL;
+  p->grad_normalize = 1;
+  p->c_cdl = 0.04;
+  p->log_capacity = 4096;
+  p->use_graphs = 1;
+}
+
+const char* fredopt_strerror(int code) {
+  const int i = -code;
+  if (i < 0 || i >= (int)(sizeof(kErrNames) / sizeof(kErrNames[0]))) return "unknown error";
+  return kErrNames[i];
+}
+
+const char* fredopt_last_error(fredopt_t h) { return h ? h->last_error.c_str() : "null handle"; }
+
+int fredopt_create(fredopt_t* out, int device, void* cuda_stream) {
+  if (!out) return FREDOPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return FREDOPT_ERR_INVALID_ARG;
+  }
+  fredopt_ctx* h = new fredopt_ctx();
+  h->device = device;
+  DeviceGuard dg(device);
+  if (init_kernels(&h->geo, device) != 0) {
+    delete h;
+    cudaGetLastError();
+    return FREDOPT_ERR_CUDA;
+  }
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+  h->l2_bytes = (size_t)l2;
+  if (cuda_stream) {
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return FREDOPT_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&h->ev_it0) != cudaSuccess || cudaEventCreate(&h->ev_it1) != cudaSuccess ||
+      h->st.alloc(1) != cudaSuccess || h->errw.alloc(1) != cudaSuccess) {
+    fredopt_destroy(h);
+    return FREDOPT_ERR_CUDA;
+  }
+  cudaMemsetAsync(h->st.p, 0, sizeof(DevState), h->stream);
+  fredopt_default_params(&h->prm);
+  h->tab.c = 0.04;
+  cudaStreamSynchronize(h->stream);
+  *out = h;
+  return FREDOPT_OK;
+}
+
+int fredopt_destroy(fredopt_t h) {
+  if (!h) return FREDOPT_ERR_INVALID_ARG;
+  DeviceGuard dg(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_graph(h);
+  for (auto& t : h->timers) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_it0) cudaEventDestroy(h->ev_it0);
+  if (h->ev_it1) cudaEventDestroy(h->ev_it1);
+  cudaStream_t own = h->own_stream ? h->stream : nullptr;
+  delete h;  // frees every device buffer
+  if (own) cudaStreamDestroy(own);
+  return FREDOPT_OK;
+}
+
+int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t nnz,
+                           const int64_t* row_ptr, const int32_t* col, const float* D_val,
+                           const float* L_val, const uint32_t* voxel_mask, int format,
+                           uint32_t flags) {
+  if (!h) return FREDOPT_ERR_INVALID_ARG;
+  const int fmt = format & 0xff;
+  const bool roi = (format & FREDOPT_ROWS_ROI) != 0;
+  if (fmt < 0 || fmt > 2 || (format & ~0x1ff))
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "format must be FP32/BF16/FP16 | ROWS_ALL/ROI");
+  if (n_vox < 0 || n_spots < 1 || nnz < 0 || nnz > 2147483647LL || n_vox > 2147483647LL)
+    return fail(h, FREDOPT_ERR_SHAPE, "need n_vox >= 0, n_spots >= 1, 0 <= nnz < 2^31");
+  if (!row_ptr || !voxel_mask || (nnz > 0 && (!col || !D_val || !L_val)))
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "null array");
+  DeviceGuard dg(h->device);
+  free_graph(h);
+  h->loaded = false;
+  h->begun = false;
+  cudaStream_t s = h->stream;
+  join_in(h);
+
+  // ---- host copies of row_ptr and the mask; row_ptr checked on the host
+  std::vector<int64_t> rp0(n_vox + 1);
+  std::vector<uint32_t> m0(n_vox);
+  if (dev_ptr(flags)) {
+    CK(cudaMemcpyAsync(rp0.data(), row_ptr, (n_vox + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (n_vox) CK(cudaMemcpyAsync(m0.data(), voxel_mask, n_vox * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(rp0.data(), row_ptr, (n_vox + 1) * sizeof(int64_t));
+    if (n_vox) std::memcpy(m0.data(), voxel_mask, n_vox * sizeof(uint32_t));
+  }
+  if (rp0[0] != 0 || rp0[n_vox] != nnz) return fail(h, FREDOPT_ERR_PATTERN, "row_ptr[0] != 0 or row_ptr[n_vox] != nnz");
+  for (int64_t i = 0; i < n_vox; ++i)
+    if (rp0[i + 1] < rp0[i]) return fail(h, FREDOPT_ERR_PATTERN, "row_ptr not monotone");
+
+  // ---- device order of rows
+  std::vector<int64_t> order;  // device row -> voxel
+  int64_t n_hot = n_vox;
+  if (roi) {
+    order.reserve(n_vox);
+    for (int64_t i = 0; i < n_vox; ++i)
+      if (m0[i]) order.push_back(i);
+    n_hot = (int64_t)order.size();
+    for (int64_t i = 0; i < n_vox; ++i)
+      if (!m0[i]) order.push_back(i);
+  }
+  std::vector<int64_t> rp1;
+  if (roi) {
+    rp1.resize(n_vox + 1);
+    rp1[0] = 0;
+    for (int64_t r = 0; r < n_vox; ++r) rp1[r + 1] = rp1[r] + (rp0[order[r] + 1] - rp0[order[r]]);
+  }
+  const std::vector<int64_t>& rpd = roi ? rp1 : rp0;
+
+  // ---- upload + validate (on the input layout)
+  DBuf<int64_t> rp_in;
+  DBuf<int32_t> col_in;
+  DBuf<float> D_in, L_in;
+  const int32_t* colp = col;
+  const float *Dp = D_val, *Lp = L_val;
+  CK(upload_vec(h, rp_in, rp0));
+  if (!dev_ptr(flags)) {
+    CK(col_in.alloc(nnz));
+    CK(D_in.alloc(nnz));
+    CK(L_in.alloc(nnz));
+    if (nnz) {
+      CK(cudaMemcpyAsync(col_in.p, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(D_in.p, D_val, nnz * sizeof(float), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(L_in.p, L_val, nnz * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    colp = col_in.p;
+    Dp = D_in.p;
+    Lp = L_in.p;
+  }
+  CK(cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
+  launch_validate(rp_in.p, colp, Dp, Lp, n_vox, n_spots, nnz, h->errw.p, s);
+  CK(cudaGetLastError());
+  int verr = 0;
+  CK(cudaMemcpyAsync(&verr, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (verr & 1) return fail(h, FREDOPT_ERR_PATTERN, "column index out of range or not strictly increasing within a row");
+  if (verr & 2) return fail(h, FREDOPT_ERR_NONFINITE, "NaN or Inf in D or L");
+
+  // ---- drop the previous plan
+  h->rp.release(); h->col.release(); h->Dv.release(); h->Lv.release(); h->sD.release(); h->sL.release();
+  h->voxel.release(); h->mask.release(); h->cp.release(); h->crow.release(); h->DTv.release(); h->LTv.release();
+
+  // ---- FP32 CSR in device order
+  DBuf<int32_t> col_d;
+  DBuf<float> D_d, L_d;
+  CK(upload_vec(h, h->rp, rpd));
+  if (roi) {
+    DBuf<int64_t> src_row;
+    CK(upload_vec(h, src_row, order));
+    CK(col_d.alloc(nnz));
+    CK(D_d.alloc(nnz));
+    CK(L_d.alloc(nnz));
+    launch_gather_rows(rp_in.p, src_row.p, h->rp.p, n_vox, colp, Dp, Lp, col_d.p, D_d.p, L_d.p, s);
+    CK(cudaGetLastError());
+    CK(upload_vec(h, h->voxel, order));
+    CK(cudaStreamSynchronize(s));
+  } else if (dev_ptr(flags)) {
+    CK(col_d.alloc(nnz));
+    CK(D_d.alloc(nnz));
+    CK(L_d.alloc(nnz));
+    if (nnz) {
+      CK(cudaMemcpyAsync(col_d.p, col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(D_d.p, D_val, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(L_d.p, L_val, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+  } else {
+    std::swap(col_d.p, col_in.p); std::swap(col_d.n, col_in.n);
+    std::swap(D_d.p, D_in.p); std::swap(D_d.n, D_in.n);
+    std::swap(L_d.p, L_in.p); std::swap(L_d.n, L_in.n);
+  }
+  CK(cudaStreamSynchronize(s));
+  col_in.release(); D_in.release(); L_in.release(); rp_in.release();
+  std::swap(h->col.p, col_d.p); std::swap(h->col.n, col_d.n);
+
+  // ---- value storage (quantised with power-of-two row scales, or FP32)
+  if (fmt == FREDOPT_FP32) {
+    h->Dv.p = reinterpret_cast<uint8_t*>(D_d.p); h->Dv.n = D_d.n * 4; D_d.p = nullptr; D_d.n = 0;
+    h->Lv.p = reinterpret_cast<uint8_t*>(L_d.p); h->Lv.n = L_d.n * 4; L_d.p = nullptr; L_d.n = 0;
+  } else {
+    CK(h->Dv.alloc((size_t)nnz * 2));
+    CK(h->Lv.alloc((size_t)nnz * 2));
+    CK(h->sD.alloc(n_vox));
+    CK(h->sL.alloc(n_vox));
+    launch_quantize(fmt, h->rp.p, n_vox, D_d.p, L_d.p, h->Dv.p, h->Lv.p, h->sD.p, h->sL.p, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    D_d.release();
+    L_d.release();
+  }
+
+  // ---- streamed rows: mask, FP64 moments
+  h->V = n_vox; h->nnz = nnz; h->n = n_spots; h->n_pad = (n_spots + 3) & ~3;
+  h->fmt = fmt; h->roi = roi; h->n_hot = n_hot; h->nnz_hot = rpd[n_hot];
+  h->h_voxel = roi ? std::vector<int64_t>(order.begin(), order.end()) : std::vector<int64_t>();
+  h->h_mask.resize(n_hot);
+  for (int64_t r = 0; r < n_hot; ++r) h->h_mask[r] = m0[roi ? order[r] : r];
+  CK(upload_vec(h, h->mask, h->h_mask));
+  CK(h->mdd.alloc(n_hot)); CK(h->mll.alloc(n_hot)); CK(h->mdl.alloc(n_hot));
+  launch_moments(fmt, h->rp.p, n_hot, h->Dv.p, h->Lv.p, fmt ? h->sD.p : nullptr, fmt ? h->sL.p : nullptr,
+                 h->mdd.p, h->mll.p, h->mdl.p, s);
+  CK(cudaGetLastError());
+
+  // ---- CSC copy of the streamed rows (blocked stable counting transpose)
+  {
+    const int n_blk = (int)std::max<int64_t>(1, std::min<int64_t>(2 * h->geo.n_sms, n_hot));
+    std::vector<int64_t> blk = partition_rows(rpd, n_hot, n_blk, 1);
+    DBuf<int64_t> blk_d, tot_d;
+    DBuf<int32_t> cnt;
+    CK(upload_vec(h, blk_d, blk));
+    CK(cnt.alloc((size_t)n_blk * n_spots));
+    CK(cudaMemsetAsync(cnt.p, 0, (size_t)n_blk * n_spots * sizeof(int32_t), s));
+    if (n_hot > 0) launch_csc_count(h->rp.p, h->col.p, blk_d.p, n_blk, n_spots, cnt.p, s);
+    CK(tot_d.alloc(n_spots));
+    launch_csc_colsum(cnt.p, n_blk, n_spots, tot_d.p, s);
+    CK(cudaGetLastError());
+    std::vector<int64_t> tot(n_spots), cph(n_spots + 1);
+    CK(cudaMemcpyAsync(tot.data(), tot_d.p, n_spots * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cph[0] = 0;
+    for (int j = 0; j < n_spots; ++j) cph[j + 1] = cph[j] + tot[j];
+    if (cph[n_spots] != h->nnz_hot) return fail(h, FREDOPT_ERR_CUDA, "CSC count mismatch");
+    CK(upload_vec(h, h->cp, cph));
+    launch_csc_offsets(cnt.p, n_blk, n_spots, h->cp.p, s);
+    const int vb = value_bytes(fmt);
+    CK(h->crow.alloc(h->nnz_hot));
+    CK(h->DTv.alloc((size_t)h->nnz_hot * vb));
+    CK(h->LTv.alloc((size_t)h->nnz_hot * vb));
+    if (n_hot > 0)
+      launch_csc_fill(fmt, h->rp.p, h->col.p, h->Dv.p, h->Lv.p, blk_d.p, n_blk, n_spots, cnt.p,
+                      h->crow.p, h->DTv.p, h->LTv.p, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+
+    // chunk schedule of the transposed product
+    const int W3 = h->geo.bwd_warps;
+    int64_t C = h->nnz_hot / ((int64_t)W3 * 8);
+    C = std::max<int64_t>(256, std::min<int64_t>(8192, C));
+    C = (C + 31) & ~31LL;
+    std::vector<int64_t> cptr;
+    std::vector<int32_t> cchunk(n_spots + 1);
+    cptr.reserve(h->nnz_hot / C + n_spots + 1);
+    for (int j = 0; j < n_spots; ++j) {
+      cchunk[j] = (int32_t)cptr.size();
+      for (int64_t p = cph[j]; p < cph[j + 1]; p += C) cptr.push_back(p);
+    }
+    cchunk[n_spots] = (int32_t)cptr.size();
+    h->n_chunks = (int64_t)cptr.size();
+    cptr.push_back(h->nnz_hot);
+    std::vector<int64_t> wch64 = partition_rows(cptr, h->n_chunks, W3, 16);
+    std::vector<int32_t> wch(wch64.begin(), wch64.end());
+    CK(upload_vec(h, h->chunk_ptr, cptr));
+    CK(upload_vec(h, h->col_chunk, cchunk));
+    CK(upload_vec(h, h->warp_chunk, wch));
+    CK(cudaStreamSynchronize(s));
+  }
+
+  // ---- row schedules of the forward product
+  {
+    std::vector<int64_t> wr = partition_rows(rpd, n_hot, h->geo.fwd_warps, 8);
+    CK(upload_vec(h, h->warp_row_hot, wr));
+    std::vector<int64_t> wa = partition_rows(rpd, n_vox, h->geo.fwd_warps, 8);
+    CK(upload_vec(h, h->warp_row_all, wa));
+    CK(cudaStreamSynchronize(s));
+  }
+  // streaming (evict-first) loads when the streamed matrices do not fit in L2
+  const double mat_bytes = (double)h->nnz_hot * (4.0 + 2.0 * value_bytes(fmt));
+  h->hint_fwd = mat_bytes > 0.5 * (double)h->l2_bytes;
+  h->hint_bwd = h->hint_fwd;
+
+  // ---- work buffers
+  CK(h->w.alloc(h->n_pad)); CK(h->g.alloc(h->n_pad)); CK(h->xbuf.alloc(h->n_pad)); CK(h->gtmp.alloc(h->n_pad));
+  CK(cudaMemsetAsync(h->w.p, 0, h->n_pad * sizeof(float), s));
+  CK(cudaMemsetAsync(h->g.p, 0, h->n_pad * sizeof(float), s));
+  CK(cudaMemsetAsync(h->xbuf.p, 0, h->n_pad * sizeof(float), s));
+  CK(cudaMemsetAsync(h->gtmp.p, 0, h->n_pad * sizeof(float), s));
+  CK(h->yw.alloc(n_hot)); CK(h->yg.alloc(n_hot)); CK(h->r.alloc(n_hot)); CK(h->gam.alloc(n_hot));
+  CK(cudaMemsetAsync(h->yg.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
+  CK(h->chunk_sum.alloc(h->n_chunks));
+  const Geometry& G = h->geo;
+  h->off_f = 0;
+  h->off_bc = h->off_f + std::max(G.fwd_warps, G.row_blocks);
+  h->off_g = h->off_bc + 2 * G.fwd_warps;
+  h->off_k2 = h->off_g + G.col_blocks;
+  h->off_fin = h->off_k2 + 3 * G.row_blocks;
+  h->off_cnt = h->off_fin + 8 * G.row_blocks;
+  h->n_part = h->off_cnt + 3 * G.row_blocks;
+  CK(h->part.alloc(h->n_part));
+  CK(cudaMemsetAsync(h->part.p, 0, h->n_part * sizeof(double), s));
+  h->y64.release(); h->yall.release(); h->fout_a.release(); h->fout_b.release();
+  h->vin_a.release(); h->vin_b.release();
+  CK(cudaStreamSynchronize(s));
+
+  h->tab.n_con = 0;
+  h->tab.n_obj = 0;
+  h->have_con = false;
+  h->obj_dose = false;
+  h->W_all = 0.0;
+  h->n_rows_reach = h->n_unreach = 0;
+  h->loaded = true;
+  return FREDOPT_OK;
+}
+
+int fredopt_set_constraints(fredopt_t h, int n, const fredopt_constraint* c) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (n < 0 || n > kMaxCon || (n > 0 && !c)) return fail(h, FREDOPT_ERR_INVALID_ARG, "0 <= n <= 32 constraints");
+  for (int i = 0; i < n; ++i) {
+    if (c[i].struct_bit >= 32 || c[i].kind < 0 || c[i].kind > 5 || !std::isfinite(c[i].bound) ||
+        !(c[i].priority > 0.0) || !std::isfinite(c[i].priority))
+      return fail(h, FREDOPT_ERR_INVALID_ARG, "constraint " + std::to_string(i) + " invalid");
+  }
+  DeviceGuard dg(h->device);
+  free_graph(h);
+  h->tab.n_con = n;
+  for (int i = 0; i < n; ++i) {
+    h->tab.con[i].bit = c[i].struct_bit;
+    h->tab.con[i].kind = c[i].kind;
+    h->tab.con[i].bound = c[i].bound;
+    h->tab.con[i].prio = c[i].priority;
+  }
+  double* pc = h->part.p + h->off_cnt;
+  launch_count_rows(h->geo, h->tab, h->mask.p, h->mdd.p, h->mll.p, h->mdl.p, h->n_hot, pc, h->stream);
+  CK(cudaGetLastError());
+  std::vector<double> hp(3 * h->geo.row_blocks);
+  CK(cudaMemcpyAsync(hp.data(), pc, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  double nr = 0, nu = 0, W = 0;
+  for (int b = 0; b < h->geo.row_blocks; ++b) {
+    nr += hp[3 * b];
+    nu += hp[3 * b + 1];
+    W += hp[3 * b + 2];
+  }
+  h->n_rows_reach = (int64_t)nr;
+  h->n_unreach = (int64_t)nu;
+  h->W_all = W;
+  h->have_con = true;
+  return FREDOPT_OK;
+}
+
+int fredopt_set_objective(fredopt_t h, int n, const fredopt_objective_term* t) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (n < 0 || n > kMaxObj || (n > 0 && !t)) return fail(h, FREDOPT_ERR_INVALID_ARG, "0 <= n <= 32 terms");
+  for (int i = 0; i < n; ++i)
+    if (t[i].struct_bit >= 32 || (t[i].quantity != FREDOPT_Q_DOSE && t[i].quantity != FREDOPT_Q_CDL) ||
+        !std::isfinite(t[i].target) || !(t[i].weight > 0.0) || !std::isfinite(t[i].weight))
+      return fail(h, FREDOPT_ERR_INVALID_ARG, "objective term " + std::to_string(i) + " invalid");
+  free_graph(h);
+  h->tab.n_obj = n;
+  h->obj_dose = false;
+  for (int i = 0; i < n; ++i) {
+    h->tab.obj[i].bit = t[i].struct_bit;
+    h->tab.obj[i].q = t[i].quantity;
+    h->tab.obj[i].target = t[i].target;
+    h->tab.obj[i].weight = t[i].weight;
+    if (t[i].quantity == FREDOPT_Q_DOSE) h->obj_dose = true;
+  }
+  return FREDOPT_OK;
+}
+
+int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
+                  const fredopt_params* params, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!w0) return fail(h, FREDOPT_ERR_INVALID_ARG, "w0 is null");
+  fredopt_params p;
+  if (params) p = *params;
+  else fredopt_default_params(&p);
+  if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FREDOPT_ERR_INVALID_ARG, "need 0 < alpha < 1");
+  if (!(relaxation > 0.0 && relaxation <= 2.0)) return fail(h, FREDOPT_ERR_INVALID_ARG, "need 0 < relaxation <= 2");
+  if (!(p.eta > 0.0 && p.eta <= 1.0)) return fail(h, FREDOPT_ERR_INVALID_ARG, "need 0 < eta <= 1");
+  if (p.reductions < 0 || p.max_trials < 1 || p.log_capacity < 0 ||
+      (p.cimmino_norm != FREDOPT_NORM_ALL && p.cimmino_norm != FREDOPT_NORM_VIOLATED) ||
+      !(p.c_cdl > 0.0) || !std::isfinite(p.beta0))
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "bad parameters");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  join_in(h);
+  std::vector<float> hw(h->n);
+  if (dev_ptr(flags)) {
+    CK(cudaMemcpyAsync(hw.data(), w0, h->n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(hw.data(), w0, h->n * sizeof(float));
+  }
+  double nrm = 0.0;
+  for (float v : hw) {
+    if (!std::isfinite(v)) return fail(h, FREDOPT_ERR_NONFINITE, "w0 not finite");
+    if (v < 0.0f) return fail(h, FREDOPT_ERR_INVALID_ARG, "w0 must be >= 0");
+    nrm += (double)v * (double)v;
+  }
+  free_graph(h);
+  h->prm = p;
+  h->alpha = alpha;
+  h->lam = relaxation;
+  h->beta0 = p.beta0 < 0.0 ? 0.1 * std::sqrt(nrm) : p.beta0;
+  h->tab.c = p.c_cdl;
+  CK(cudaMemcpyAsync(h->w.p, hw.data(), h->n * sizeof(float), cudaMemcpyHostToDevice, s));
+  CK(h->log.alloc(std::max(1, p.log_capacity)));
+  DevState& d = h->st_host;
+  std::memset(&d, 0, sizeof(d));
+  d.beta0 = h->beta0;
+  d.alpha = alpha;
+  d.lam = relaxation;
+  d.eta = p.eta;
+  d.W_all = h->W_all;
+  d.reductions = p.reductions;
+  d.max_trials = p.max_trials;
+  d.norm = p.cimmino_norm;
+  d.grad_normalize = p.grad_normalize ? 1 : 0;
+  d.log_cap = p.log_capacity;
+  CK(cudaMemcpyAsync(h->st.p, &d, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  h->iters_run = 0;
+  h->device_ms = 0.0;
+  h->it_pending = false;
+  if (p.use_graphs && !h->timing) {
+    const int64_t before = h->launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(h);
+    cudaError_t e = cudaStreamEndCapture(s, &h->graph);
+    if (e != cudaSuccess) {
+      h->graph = nullptr;
+      return cuda_fail(h, e, "graph capture");
+    }
+    h->graph_nodes = (int)(h->launches - before);
+    h->launches = before;
+    CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+  }
+  CK(cudaStreamSynchronize(s));
+  h->begun = true;
+  return FREDOPT_OK;
+}
+
+int fredopt_iterate(fredopt_t h, int iters) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!h->begun) return fail(h, FREDOPT_ERR_NOT_LOADED, "call fredopt_begin first");
+  if (iters < 0) return fail(h, FREDOPT_ERR_INVALID_ARG, "iters < 0");
+  if (iters == 0) return FREDOPT_OK;
+  DeviceGuard dg(h->device);
+  if (h->it_pending) {
+    float ms = 0.f;
+    CK(cudaEventSynchronize(h->ev_it1));
+    if (cudaEventElapsedTime(&ms, h->ev_it0, h->ev_it1) == cudaSuccess) h->device_ms += ms;
+    h->it_pending = false;
+  }
+  CK(cudaEventRecord(h->ev_it0, h->stream));
+  for (int i = 0; i < iters; ++i) {
+    if (h->gexec && !h->timing) {
+      CK(cudaGraphLaunch(h->gexec, h->stream));
+      h->launches += h->graph_nodes;
+    } else {
+      enqueue_iteration(h);
+      CK(cudaGetLastError());
+    }
+  }
+  CK(cudaEventRecord(h->ev_it1, h->stream));
+  h->it_pending = true;
+  h->iters_run += iters;
+  return FREDOPT_OK;
+}
+
+int fredopt_end(fredopt_t h, float* w_out, float* dose_out, float* letd_out, fredopt_report* rep,
+                uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!h->begun) return fail(h, FREDOPT_ERR_NOT_LOADED, "call fredopt_begin first");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  const Geometry& G = h->geo;
+  if (h->it_pending) {
+    float ms = 0.f;
+    CK(cudaEventSynchronize(h->ev_it1));
+    if (cudaEventElapsedTime(&ms, h->ev_it0, h->ev_it1) == cudaSuccess) h->device_ms += ms;
+    h->it_pending = false;
+  }
+  // final FP64-accumulated product over every row
+  CK(h->y64.ensure(std::max<int64_t>(1, h->V)));
+  float* dptr = nullptr;
+  float* lptr = nullptr;
+  if (dose_out || letd_out) {
+    if (dev_ptr(flags)) {
+      dptr = dose_out;
+      lptr = letd_out;
+    } else {
+      CK(h->fout_a.ensure(std::max<int64_t>(1, h->V)));
+      CK(h->fout_b.ensure(std::max<int64_t>(1, h->V)));
+      dptr = dose_out ? h->fout_a.p : nullptr;
+      lptr = letd_out ? h->fout_b.p : nullptr;
+    }
+  }
+  FwdArgs fa = fwd_args(h, false);
+  fa.x = h->w.p;
+  fa.y64 = h->y64.p;
+  fa.dose_out = dptr;
+  fa.letd_out = lptr;
+  run(h, 0, [&] { launch_forward(G, h->fmt, EPI_FINAL, false, fa, h->tab, s); });
+  double* pf = h->part.p + h->off_fin;
+  run(h, 5, [&] { launch_final_check(G, h->tab, h->y64.p, h->mask.p, h->mdd.p, h->mll.p, h->mdl.p, h->n_hot, pf, s); });
+  CK(cudaGetLastError());
+  std::vector<double> hp(8 * G.row_blocks);
+  CK(cudaMemcpyAsync(hp.data(), pf, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DevState d;
+  CK(cudaMemcpyAsync(&d, h->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(copy_out(h, w_out, h->w.p, (size_t)h->n * sizeof(float), flags));
+  if (!dev_ptr(flags)) {
+    if (dose_out) CK(cudaMemcpyAsync(dose_out, h->fout_a.p, h->V * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (letd_out) CK(cudaMemcpyAsync(letd_out, h->fout_b.p, h->V * sizeof(float), cudaMemcpyDeviceToHost, s));
+  }
+  rc = check_sticky(h);
+  collect_timers(h);
+  if (rc) return rc;
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->iters = h->iters_run;
+    rep->s = d.s;
+    rep->accepted = d.accepted_total;
+    rep->n_rows = h->n_rows_reach;
+    rep->unreachable_rows = h->n_unreach;
+    double nv = 0.0, f = 0.0;
+    for (int b = 0; b < G.row_blocks; ++b) {
+      for (int q = 0; q < 6; ++q) rep->max_violation[q] = std::max(rep->max_violation[q], hp[8 * b + q]);
+      nv += hp[8 * b + 6];
+      f += hp[8 * b + 7];
+    }
+    rep->n_violated = (int64_t)nv;
+    rep->objective = f;
+    rep->beta0 = h->beta0;
+    rep->device_ms = h->device_ms;
+  }
+  return FREDOPT_OK;
+}
+
+int fredopt_superiorize(fredopt_t h, const float* w0, int iters, double alpha, double relaxation,
+                        const fredopt_params* params, float* w_out, float* dose_out,
+                        float* letd_out, fredopt_report* rep, uint32_t flags) {
+  int rc = fredopt_begin(h, w0, alpha, relaxation, params, flags);
+  if (rc) return rc;
+  rc = fredopt_iterate(h, iters);
+  if (rc) return rc;
+  return fredopt_end(h, w_out, dose_out, letd_out, rep, flags);
+}
+
+int fredopt_get_log(fredopt_t h, fredopt_log_entry* out, int max_entries) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!h->begun) return fail(h, FREDOPT_ERR_NOT_LOADED, "no solve begun");
+  if (max_entries < 0 || (max_entries > 0 && !out)) return fail(h, FREDOPT_ERR_INVALID_ARG, "bad output");
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  DevState d;
+  CK(cudaMemcpy(&d, h->st.p, sizeof(DevState), cudaMemcpyDeviceToHost));
+  const int cap = h->prm.log_capacity;
+  if (cap <= 0) return 0;
+  const int64_t k = d.k;
+  const int64_t first = std::max<int64_t>(0, k - cap);
+  const int cnt = (int)std::min<int64_t>(k - first, max_entries);
+  std::vector<LogEntry> all(cap);
+  CK(cudaMemcpy(all.data(), h->log.p, cap * sizeof(LogEntry), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < cnt; ++i) {
+    const LogEntry& e = all[(first + i) % cap];
+    out[i].k = e.k;
+    out[i].s = e.s;
+    out[i].accepted = e.accepted;
+    out[i].n_violated = e.n_violated;
+    out[i].beta = e.beta;
+    out[i].f_start = e.f_start;
+    out[i].f_end = e.f_end;
+    out[i].gnorm = e.gnorm;
+    out[i].max_violation = e.max_violation;
+  }
+  return cnt;
+}
+
+int fredopt_get_state(fredopt_t h, float* w, int64_t* k, int64_t* s, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!h->begun) return fail(h, FREDOPT_ERR_NOT_LOADED, "no solve begun");
+  DeviceGuard dg(h->device);
+  DevState d;
+  CK(cudaMemcpyAsync(&d, h->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  if (w) CK(copy_out(h, w, h->w.p, (size_t)h->n * sizeof(float), flags));
+  rc = check_sticky(h);
+  if (rc) return rc;
+  if (k) *k = d.k;
+  if (s) *s = d.s;
+  return FREDOPT_OK;
+}
+
+int fredopt_set_state(fredopt_t h, const float* w, int64_t k, int64_t s, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!h->begun) return fail(h, FREDOPT_ERR_NOT_LOADED, "call fredopt_begin first");
+  if (!w || k < 0 || s < 0) return fail(h, FREDOPT_ERR_INVALID_ARG, "bad state");
+  DeviceGuard dg(h->device);
+  join_in(h);
+  CK(cudaStreamSynchronize(h->stream));
+  DevState d;
+  CK(cudaMemcpy(&d, h->st.p, sizeof(DevState), cudaMemcpyDeviceToHost));
+  d.k = k;
+  d.s = s;
+  d.done = 0u;
+  CK(copy_in(h, h->w.p, w, (size_t)h->n * sizeof(float), flags));
+  h->st_host = d;
+  CK(cudaMemcpyAsync(h->st.p, &h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FREDOPT_OK;
+}
+
+int fredopt_forward(fredopt_t h, const float* w, float* dose_out, float* lw_out, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!w) return fail(h, FREDOPT_ERR_INVALID_ARG, "w is null");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  join_in(h);
+  rc = load_spot_vec(h, h->xbuf, w, flags);
+  if (rc) return rc;
+  CK(h->yall.ensure(std::max<int64_t>(1, h->V)));
+  FwdArgs fa = fwd_args(h, false);
+  fa.x = h->xbuf.p;
+  fa.y = h->yall.p;
+  run(h, 0, [&] { launch_forward(h->geo, h->fmt, EPI_STORE, h->hint_fwd, fa, h->tab, s); });
+  float *da = dose_out, *db = lw_out;
+  if (!dev_ptr(flags)) {
+    CK(h->fout_a.ensure(std::max<int64_t>(1, h->V)));
+    CK(h->fout_b.ensure(std::max<int64_t>(1, h->V)));
+    da = dose_out ? h->fout_a.p : nullptr;
+    db = lw_out ? h->fout_b.p : nullptr;
+  }
+  launch_scatter_y(h->yall.p, h->roi ? h->voxel.p : nullptr, h->V, da, db, s);
+  CK(cudaGetLastError());
+  if (!dev_ptr(flags)) {
+    if (dose_out) CK(cudaMemcpyAsync(dose_out, h->fout_a.p, h->V * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (lw_out) CK(cudaMemcpyAsync(lw_out, h->fout_b.p, h->V * sizeof(float), cudaMemcpyDeviceToHost, s));
+  }
+  rc = check_sticky(h);
+  collect_timers(h);
+  return rc;
+}
+
+int fredopt_backward(fredopt_t h, const float* a_D, const float* a_L, float* u_out, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!u_out) return fail(h, FREDOPT_ERR_INVALID_ARG, "u_out is null");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  join_in(h);
+  const float *pa = a_D, *pb = a_L;
+  if (!dev_ptr(flags)) {
+    CK(h->vin_a.ensure(std::max<int64_t>(1, h->V)));
+    CK(h->vin_b.ensure(std::max<int64_t>(1, h->V)));
+    if (a_D) CK(cudaMemcpyAsync(h->vin_a.p, a_D, h->V * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (a_L) CK(cudaMemcpyAsync(h->vin_b.p, a_L, h->V * sizeof(float), cudaMemcpyHostToDevice, s));
+    pa = a_D ? h->vin_a.p : nullptr;
+    pb = a_L ? h->vin_b.p : nullptr;
+  }
+  launch_scale_coef(h->n_hot, pa, pb, h->roi ? h->voxel.p : nullptr, h->fmt ? h->sD.p : nullptr,
+                    h->fmt ? h->sL.p : nullptr, h->gam.p, s);
+  BwdArgs ba = bwd_args(h, h->gam.p);
+  run(h, 1, [&] { launch_backward(h->geo, h->fmt, h->hint_bwd, true, ba, s); });
+  ColArgs ca = col_args(h);
+  ca.out = h->gtmp.p;
+  run(h, 3, [&] { launch_colfinish(h->geo, COL_OUT, ca, s); });
+  CK(cudaGetLastError());
+  CK(copy_out(h, u_out, h->gtmp.p, (size_t)h->n * sizeof(float), flags));
+  rc = check_sticky(h);
+  collect_timers(h);
+  return rc;
+}
+
+int fredopt_feasibility_step(fredopt_t h, const float* x, double relaxation, double prio_scale,
+                             int norm, float* w_out, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!h->have_con) return fail(h, FREDOPT_ERR_NOT_LOADED, "no constraints set");
+  if (!x || !w_out || !(relaxation > 0.0 && relaxation <= 2.0) || !(prio_scale > 0.0) ||
+      (norm != FREDOPT_NORM_ALL && norm != FREDOPT_NORM_VIOLATED))
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  const Geometry& G = h->geo;
+  join_in(h);
+  rc = load_spot_vec(h, h->xbuf, x, flags);
+  if (rc) return rc;
+  FwdArgs fa = fwd_args(h, true);
+  fa.x = h->xbuf.p;
+  fa.y = h->yw.p;
+  run(h, 0, [&] { launch_forward(G, h->fmt, EPI_STORE, h->hint_fwd, fa, h->tab, s); });
+  ConArgs k2 = con_args(h);
+  run(h, 2, [&] { launch_constraints(G, h->tab, k2, s); });
+  if (h->tab.n_con > 0) {
+    BwdArgs bb = bwd_args(h, h->gam.p);
+    run(h, 1, [&] { launch_backward(G, h->fmt, h->hint_bwd, true, bb, s); });
+  }
+  ColArgs cc = col_args(h);
+  cc.w = h->xbuf.p;
+  cc.use_u = h->tab.n_con > 0 ? 1 : 0;
+  cc.norm = norm;
+  cc.lam = relaxation;
+  cc.prio_scale = prio_scale;
+  cc.in_solve = 0;
+  run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
+  CK(cudaGetLastError());
+  CK(copy_out(h, w_out, h->xbuf.p, (size_t)h->n * sizeof(float), flags));
+  rc = check_sticky(h);
+  collect_timers(h);
+  return rc;
+}
+
+int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_out, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!x) return fail(h, FREDOPT_ERR_INVALID_ARG, "x is null");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  const Geometry& G = h->geo;
+  join_in(h);
+  rc = load_spot_vec(h, h->xbuf, x, flags);
+  if (rc) return rc;
+  double* part_f = h->part.p + h->off_f;
+  FwdArgs fa = fwd_args(h, true);
+  fa.x = h->xbuf.p;
+  fa.y = h->yw.p;
+  fa.r_out = h->r.p;
+  fa.part = part_f;
+  run(h, 0, [&] { launch_forward(G, h->fmt, EPI_OBJ, h->hint_fwd, fa, h->tab, s); });
+  BwdArgs ba = bwd_args(h, h->r.p);
+  run(h, 1, [&] { launch_backward(G, h->fmt, h->hint_bwd, h->obj_dose, ba, s); });
+  ColArgs ca = col_args(h);
+  ca.out = h->gtmp.p;
+  ca.part = h->part.p + h->off_g;
+  run(h, 3, [&] { launch_colfinish(G, COL_GRAD, ca, s); });
+  CK(cudaGetLastError());
+  std::vector<double> hp(G.fwd_warps);
+  CK(cudaMemcpyAsync(hp.data(), part_f, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (grad_out) CK(copy_out(h, grad_out, h->gtmp.p, (size_t)h->n * sizeof(float), flags));
+  rc = check_sticky(h);
+  collect_timers(h);
+  if (rc) return rc;
+  if (f_out) {
+    double f = 0.0;
+    for (double v : hp) f += v;
+    *f_out = f;
+  }
+  return FREDOPT_OK;
+}
+
+int fredopt_get_sizes(fredopt_t h, int64_t* n_vox, int64_t* n_spots, int64_t* nnz, int64_t* n_rows,
+                      int64_t* nnz_rows) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (n_vox) *n_vox = h->V;
+  if (n_spots) *n_spots = h->n;
+  if (nnz) *nnz = h->nnz;
+  if (n_rows) *n_rows = h->n_hot;
+  if (nnz_rows) *nnz_rows = h->nnz_hot;
+  return FREDOPT_OK;
+}
+
+int fredopt_get_rows(fredopt_t h, int64_t* voxel, uint32_t* mask) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  DeviceGuard dg(h->device);
+  if (voxel) {
+    if (h->roi) {
+      CK(cudaMemcpy(voxel, h->voxel.p, h->n_hot * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    } else {
+      for (int64_t i = 0; i < h->n_hot; ++i) voxel[i] = i;
+    }
+  }
+  if (mask && h->n_hot) CK(cudaMemcpy(mask, h->mask.p, h->n_hot * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  return FREDOPT_OK;
+}
+
+int fredopt_get_csc(fredopt_t h, int64_t* col_ptr, int32_t* row, float* D_val, float* L_val) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  if (col_ptr) CK(cudaMemcpyAsync(col_ptr, h->cp.p, (h->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (row && h->nnz_hot) CK(cudaMemcpyAsync(row, h->crow.p, h->nnz_hot * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if ((D_val || L_val) && h->nnz_hot) {
+    DBuf<float> a, b;
+    CK(a.alloc(h->nnz_hot));
+    CK(b.alloc(h->nnz_hot));
+    launch_dequant_csc(h->fmt, h->cp.p, h->n, h->crow.p, h->DTv.p, h->LTv.p, h->fmt ? h->sD.p : nullptr,
+                       h->fmt ? h->sL.p : nullptr, a.p, b.p, s);
+    CK(cudaGetLastError());
+    if (D_val) CK(cudaMemcpyAsync(D_val, a.p, h->nnz_hot * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (L_val) CK(cudaMemcpyAsync(L_val, b.p, h->nnz_hot * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return FREDOPT_OK;
+}
+
+int fredopt_get_moments(fredopt_t h, double* dd, double* ll, double* dl) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->n_hot == 0) return FREDOPT_OK;
+  if (dd) CK(cudaMemcpy(dd, h->mdd.p, h->n_hot * sizeof(double), cudaMemcpyDeviceToHost));
+  if (ll) CK(cudaMemcpy(ll, h->mll.p, h->n_hot * sizeof(double), cudaMemcpyDeviceToHost));
+  if (dl) CK(cudaMemcpy(dl, h->mdl.p, h->n_hot * sizeof(double), cudaMemcpyDeviceToHost));
+  return FREDOPT_OK;
+}
+
+int fredopt_set_timing(fredopt_t h, int enable) {
+  if (!h) return FREDOPT_ERR_INVALID_ARG;
+  DeviceGuard dg(h->device);
+  collect_timers(h);
+  h->timing = enable != 0;
+  for (int i = 0; i < FREDOPT_KCLASS_N; ++i) {
+    h->kms[i] = 0.0;
+    h->klaunch[i] = 0;
+  }
+  h->launches = 0;
+  return FREDOPT_OK;
+}
+
+int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches) {
+  if (!h) return FREDOPT_ERR_INVALID_ARG;
+  DeviceGuard dg(h->device);
+  collect_timers(h);
+  for (int i = 0; i < FREDOPT_KCLASS_N; ++i) {
+    if (ms) ms[i] = h->kms[i];
+    if (launches) launches[i] = h->klaunch[i];
+  }
+  return FREDOPT_OK;
+}
+
+int64_t fredopt_launch_count(fredopt_t h) { return h ? h->launches : -1; }
+
+}  // extern "C"

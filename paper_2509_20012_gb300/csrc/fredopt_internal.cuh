@@ -1,0 +1,212 @@
+// Internal declarations shared by the kernels and the C ABI of libfredopt.
+// Device data layout (all in HBM, device order of rows = "streamed rows"
+// first, then the rest; see fredopt_api.cu):
+//   CSR   rp int64[V+1], col int32[nnz], Dv/Lv VT[nnz], sD/sL float[V] (16-bit only)
+//   CSC   cp int64[n+1], row int32[nnz_hot] (index of a streamed row), DTv/LTv VT[nnz_hot]
+//   rows  voxel int64[V] (device row -> voxel), mask uint32[n_hot],
+//         FP64 moments |D_i|^2, |L_i|^2, <D_i,L_i> [n_hot]
+//   state w/g float[n], yw/yg/r/gam float2[n_hot], chunk_sum float[n_chunks],
+//         per-warp/per-block FP64 partials, DevState, log ring
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace fo {
+
+constexpr int kMaxCon = 32;
+constexpr int kMaxObj = 32;
+
+// constraint kinds (same numbering as the public header)
+enum Kind { DOSE_MIN = 0, DOSE_MAX = 1, CDL_MIN = 2, CDL_MAX = 3, LETD_MIN = 4, LETD_MAX = 5 };
+
+struct ConEntry {
+  uint32_t bit;
+  int32_t kind;
+  double bound;
+  double prio;
+};
+struct ObjEntry {
+  uint32_t bit;
+  int32_t q;  // 0 dose, 1 cDL
+  double target;
+  double weight;
+};
+struct Tables {
+  int32_t n_con;
+  int32_t n_obj;
+  double c;  // cDL constant
+  ConEntry con[kMaxCon];
+  ObjEntry obj[kMaxObj];
+};
+
+// device-resident scalars of a solve
+struct DevState {
+  double coef;        // perturbed point x = w + coef * g
+  double beta0, alpha, lam, eta, W_all;
+  double f_start, f_cur, gnorm, beta_acc;
+  long long k, s, accepted_total;
+  int accepted;       // accepted steps in the current iteration
+  int reductions, max_trials, norm, grad_normalize, log_cap;
+  int err;            // bit 0: bulk-copy wait timed out
+  unsigned int done;  // last-block counter of the column finish
+  int pad;
+};
+
+struct LogEntry {
+  long long k, s;
+  int accepted, n_violated;
+  double beta, f_start, f_end, gnorm, max_violation;
+};
+
+// epilogue modes of the forward product
+enum FwdEpi { EPI_STORE = 0, EPI_OBJ = 1, EPI_BC = 2, EPI_FINAL = 3 };
+// modes of the column finish
+enum ColMode { COL_OUT = 0, COL_GRAD = 1, COL_PROJ = 2 };
+
+struct FwdArgs {
+  const int64_t* rp;
+  const int32_t* col;
+  const void* Dv;
+  const void* Lv;
+  const float* sD;       // row scales (16-bit storage) or null
+  const float* sL;
+  const int64_t* warp_row;  // [n_warps + 1]
+  const float* x;
+  int32_t n_x;           // number of spots
+  int32_t n_x_pad;       // padded to a multiple of 4 (bulk-copy size)
+  float2* y;             // (Dx, Lx) per row, FP32 (EPI_STORE/OBJ/BC)
+  const uint32_t* mask;  // per streamed row
+  int64_t n_hot;
+  float2* r_out;         // EPI_OBJ: objective residual, scaled for the CSC
+  const float2* r_in;    // EPI_BC: residual of EPI_OBJ
+  double* part;          // per-warp partials, stride n_warps: [f] or [B', C']
+  int32_t n_warps;
+  DevState* st;
+  // EPI_FINAL
+  double2* y64;
+  const int64_t* voxel;  // device row -> voxel or null (identity)
+  float* dose_out;
+  float* letd_out;
+};
+
+struct BwdArgs {
+  const int32_t* row;
+  const void* Dv;
+  const void* Lv;
+  const int64_t* chunk_ptr;   // [n_chunks + 1]
+  const int32_t* warp_chunk;  // [n_warps + 1]
+  const float2* coef;         // per streamed row
+  float* chunk_sum;
+  int32_t n_warps;
+};
+
+struct ColArgs {
+  const int32_t* col_chunk;  // [n + 1]
+  const float* chunk_sum;
+  int32_t n;
+  float* out;                // COL_OUT / COL_GRAD (g)
+  float* w;                  // COL_PROJ: updated in place
+  const float* g;            // COL_PROJ: gradient for the perturbed point
+  double* part;              // per-block partials (COL_GRAD: ||g||^2)
+  const double* k2part;      // COL_PROJ: constraint-evaluation partials
+  int32_t k2_blocks;
+  int32_t use_coef;          // COL_PROJ: 1 if x = w + coef*g
+  double prio_scale;         // COL_PROJ outside a solve (feasibility step)
+  int32_t norm;              // FREDOPT_NORM_*
+  double lam;
+  double W_all;
+  int32_t in_solve;          // COL_PROJ: 1 = scale from DevState (eta^k) and advance k
+  int32_t use_u;             // 0: no transposed product (no constraints): u = 0
+  DevState* st;
+  LogEntry* log;
+};
+
+struct ConArgs {
+  const float2* yw;     // (Dw, Lw)
+  const float2* yg;     // (Dg, Lg) or null
+  const uint32_t* mask;
+  const double* dd;
+  const double* ll;
+  const double* dl;
+  const float* sD;
+  const float* sL;
+  int64_t n_hot;
+  float2* gam;
+  double* part;         // per-block: [sum p violated, n violated, max violation]
+  int32_t use_coef;
+  DevState* st;
+};
+
+// ---------------------------------------------------------------- launches
+// (implemented in fredopt_kernels.cu; all asynchronous on `s`)
+
+struct Geometry {
+  int n_sms;
+  int fwd_threads;      // 1024
+  int fwd_blocks;       // n_sms
+  int fwd_warps;
+  int bwd_threads;      // 256
+  int bwd_blocks;
+  int bwd_warps;
+  int row_threads;      // 256
+  int row_blocks;       // constraint kernel blocks
+  int col_threads;      // 256
+  int col_blocks;
+  size_t smem_limit;    // bytes of opt-in shared memory per block
+};
+
+int init_kernels(Geometry* g, int device);  // sets function attributes once per device
+
+bool forward_uses_smem(const Geometry& g, int n_x_pad);
+void launch_forward(const Geometry& g, int fmt, int epi, bool stream_hint, const FwdArgs& a,
+                    const Tables& t, cudaStream_t s);
+void launch_backward(const Geometry& g, int fmt, bool stream_hint, bool use_D, const BwdArgs& a,
+                     cudaStream_t s);
+void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_t s);
+void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s);
+void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
+                   const double* part_g, int ng, DevState* st, cudaStream_t s);
+void launch_count_rows(const Geometry& g, const Tables& t, const uint32_t* mask, const double* dd,
+                       const double* ll, const double* dl, int64_t n_hot, double* part,
+                       cudaStream_t s);
+void launch_scatter_y(const float2* y, const int64_t* voxel, int64_t n, float* a, float* b,
+                      cudaStream_t s);
+void launch_apply_step(int64_t n_hot, int n, float* w, const float* g, float2* yw, const float2* yg,
+                       const DevState* st, cudaStream_t s);
+void launch_row_objective(const Geometry& g, const Tables& t, const float2* yw, const uint32_t* mask,
+                          const float* sD, const float* sL, int64_t n_hot, float2* r_out,
+                          double* part, cudaStream_t s);
+void launch_final_check(const Geometry& g, const Tables& t, const double2* y64, const uint32_t* mask,
+                        const double* dd, const double* ll, const double* dl, int64_t n_hot,
+                        double* part, cudaStream_t s);
+void launch_begin_state(DevState* st, cudaStream_t s);
+
+// setup (K5)
+void launch_validate(const int64_t* rp, const int32_t* col, const float* D, const float* L,
+                     int64_t n_rows, int32_t n_cols, int64_t nnz, int* err, cudaStream_t s);
+void launch_gather_rows(const int64_t* rp_src, const int64_t* src_row, const int64_t* rp_dst,
+                        int64_t n_rows, const int32_t* col_src, const float* D_src,
+                        const float* L_src, int32_t* col_dst, float* D_dst, float* L_dst,
+                        cudaStream_t s);
+void launch_quantize(int fmt, const int64_t* rp, int64_t n_rows, const float* D, const float* L,
+                     void* qD, void* qL, float* sD, float* sL, cudaStream_t s);
+void launch_moments(int fmt, const int64_t* rp, int64_t n_rows, const void* Dv, const void* Lv,
+                    const float* sD, const float* sL, double* dd, double* ll, double* dl,
+                    cudaStream_t s);
+// blocked stable counting transpose of rows [0, n_rows)
+void launch_csc_count(const int64_t* rp, const int32_t* col, const int64_t* blk_row, int n_blk,
+                      int32_t n_cols, int32_t* cnt, cudaStream_t s);
+void launch_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int64_t* cp, cudaStream_t s);
+void launch_csc_fill(int fmt, const int64_t* rp, const int32_t* col, const void* Dv, const void* Lv,
+                     const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor,
+                     int32_t* row_out, void* DT, void* LT, cudaStream_t s);
+void launch_csc_colsum(const int32_t* cnt, int n_blk, int32_t n_cols, int64_t* tot, cudaStream_t s);
+void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_t* row, const void* DT,
+                        const void* LT, const float* sD, const float* sL, float* Dout, float* Lout,
+                        cudaStream_t s);
+void launch_scale_coef(int64_t n, const float* aD, const float* aL, const int64_t* voxel,
+                       const float* sD, const float* sL, float2* coef, cudaStream_t s);
+
+}  // namespace fo

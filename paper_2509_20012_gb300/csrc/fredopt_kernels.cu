@@ -1,0 +1,1194 @@
+// Kernels of the superiorized simultaneous feasibility-seeking loop
+// (arXiv 2509.20012, Sec. 2.4.3: Fig. 2 in simultaneous form, Fig. 3, Eq. 2)
+// for sm_103a.  Memory-bound sparse work: no tensor cores.
+//
+//   K1 k_forward     fused Dx / Lx over one shared CSR index stream, 16-byte
+//                    streaming loads of col / D / L, x staged in shared
+//                    memory by one bulk (TMA) copy, warp per row, rows
+//                    assigned to warps in nnz-balanced contiguous ranges;
+//                    fused epilogues: objective residual (Eq. 2), line-search
+//                    coefficients, FP64 final outputs.
+//   K2 k_constraints per-row half-space evaluation and relaxed projection
+//                    coefficients (Fig. 2), FP64 norms and divides.
+//   K3 k_backward    transposed product over the CSC copy, split into
+//                    fixed-size column chunks, one warp per chunk range;
+//                    every chunk sum is a fixed-order warp reduction (no
+//                    float atomics, deterministic).
+//   K3b k_colfinish  per spot: sum of its chunks in order, then the
+//                    gradient, or the clip w <- max(0, x + u) (Fig. 2, last
+//                    loop); advances the iteration counter.
+//   K4 k_finish      one block: deterministic reduction of the partials and
+//                    the closed-form non-ascent trial loop (Fig. 3).
+//   K5 setup         validation, row gather, quantisation, FP64 moments,
+//                    blocked stable counting transpose (CSR -> CSC).
+#include "fredopt_internal.cuh"
+
+#include <cstdio>
+#include <type_traits>
+
+namespace fo {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kFwdThreads = 1024;
+constexpr int kBwdThreads = 256;
+constexpr int kRowThreads = 256;
+constexpr int kColThreads = 256;
+constexpr int kMbarSpins = 1 << 22;
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+template <typename VT> struct VecOf;
+template <> struct VecOf<float> { static constexpr int V = 4; };
+template <> struct VecOf<__nv_bfloat16> { static constexpr int V = 8; };
+template <> struct VecOf<__half> { static constexpr int V = 8; };
+
+template <bool S>
+__device__ __forceinline__ int4 ld16(const int4* p) {
+  if (S) return __ldcs(p);
+  return __ldg(p);
+}
+template <bool S>
+__device__ __forceinline__ uint4 ld16(const uint4* p) {
+  if (S) return __ldcs(p);
+  return __ldg(p);
+}
+
+__device__ __forceinline__ void unpack(float, uint4 u, float* o) {
+  o[0] = __uint_as_float(u.x);
+  o[1] = __uint_as_float(u.y);
+  o[2] = __uint_as_float(u.z);
+  o[3] = __uint_as_float(u.w);
+}
+__device__ __forceinline__ void unpack(__nv_bfloat16, uint4 u, float* o) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    o[2 * i] = __uint_as_float(w[i] << 16);
+    o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+__device__ __forceinline__ void unpack(__half, uint4 u, float* o) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __half2 h = *reinterpret_cast<const __half2*>(&w[i]);
+    float2 f = __half22float2(h);
+    o[2 * i] = f.x;
+    o[2 * i + 1] = f.y;
+  }
+}
+
+template <int V, bool S>
+__device__ __forceinline__ void load_cols(const int32_t* p, int* c) {
+  const int4 a = ld16<S>(reinterpret_cast<const int4*>(p));
+  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+  if (V == 8) {
+    const int4 b = ld16<S>(reinterpret_cast<const int4*>(p) + 1);
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// ---- mbarrier + bulk copy (TMA engine, non-tensor form) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// bounded wait on phase `parity`; true when the phase completed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_spins) {
+  const uint32_t a = smem_u32(bar);
+  for (int i = 0; i < max_spins; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ K1
+
+// One row: warp-wide dot products of the D and L rows with x (all lanes
+// return the totals).  Elements [s, e) of the shared index stream.
+template <typename VT, typename Acc, bool S>
+__device__ __forceinline__ void row_dot(const int32_t* __restrict__ col, const VT* __restrict__ Dv,
+                                        const VT* __restrict__ Lv, int64_t s, int64_t e,
+                                        const float* __restrict__ x, int lane, Acc& oD, Acc& oL) {
+  constexpr int V = VecOf<VT>::V;
+  int64_t a = (s + V - 1) & ~(int64_t)(V - 1);
+  if (a > e) a = e;
+  const int64_t ev = a + ((e - a) & ~(int64_t)(V - 1));
+  Acc d = 0, l = 0;
+  {
+    const int64_t p = s + lane;
+    if (p < a) {
+      const float xv = x[col[p]];
+      d += (Acc)to_f(Dv[p]) * (Acc)xv;
+      l += (Acc)to_f(Lv[p]) * (Acc)xv;
+    }
+  }
+  int64_t p = a + (int64_t)lane * V;
+  for (; p + 32 * V < ev; p += 64 * V) {
+    int c0[V], c1[V];
+    float d0[V], d1[V], l0[V], l1[V];
+    load_cols<V, S>(col + p, c0);
+    load_cols<V, S>(col + p + 32 * V, c1);
+    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
+    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p + 32 * V)), d1);
+    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
+    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p + 32 * V)), l1);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const float xv = x[c0[q]];
+      d = fma((Acc)d0[q], (Acc)xv, d);
+      l = fma((Acc)l0[q], (Acc)xv, l);
+    }
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const float xv = x[c1[q]];
+      d = fma((Acc)d1[q], (Acc)xv, d);
+      l = fma((Acc)l1[q], (Acc)xv, l);
+    }
+  }
+  if (p < ev) {
+    int c0[V];
+    float d0[V], l0[V];
+    load_cols<V, S>(col + p, c0);
+    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
+    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const float xv = x[c0[q]];
+      d = fma((Acc)d0[q], (Acc)xv, d);
+      l = fma((Acc)l0[q], (Acc)xv, l);
+    }
+  }
+  {
+    const int64_t t = ev + lane;
+    if (t < e) {
+      const float xv = x[col[t]];
+      d += (Acc)to_f(Dv[t]) * (Acc)xv;
+      l += (Acc)to_f(Lv[t]) * (Acc)xv;
+    }
+  }
+  oD = warp_sum(d);
+  oL = warp_sum(l);
+}
+
+// Objective of one row (Eq. 2 terms of the structures the voxel is in):
+// f_i = sum w (q - T)^2 ; residual rD = sum_DOSE 2w(Dx - T), rL = sum_CDL 2wc(cLx - T).
+__device__ __forceinline__ void row_objective(const Tables& t, uint32_t m, double Dx, double Lx,
+                                              double& f, double& rD, double& rL) {
+  f = 0.0; rD = 0.0; rL = 0.0;
+  for (int i = 0; i < t.n_obj; ++i) {
+    const ObjEntry& o = t.obj[i];
+    if (!((m >> o.bit) & 1u)) continue;
+    if (o.q == 0) {
+      const double d = Dx - o.target;
+      f += o.weight * d * d;
+      rD += 2.0 * o.weight * d;
+    } else {
+      const double d = t.c * Lx - o.target;
+      f += o.weight * d * d;
+      rL += 2.0 * o.weight * t.c * d;
+    }
+  }
+}
+
+template <typename VT, int EPI, bool XS, bool S>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_forward(FwdArgs a, Tables t) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using Acc = typename std::conditional<EPI == EPI_FINAL, double, float>::type;
+  const float* __restrict__ x = a.x;
+  if (XS) {
+    float* xs = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)a.n_x_pad * sizeof(float));
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    const uint32_t bytes = (uint32_t)a.n_x_pad * (uint32_t)sizeof(float);
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(xs, a.x, bytes, bar);
+    }
+    if (!mbar_wait(bar, 0, kMbarSpins)) {
+      if (threadIdx.x == 0) atomicOr(&a.st->err, 1);
+      mbar_wait(bar, 0, kMbarSpins);  // let the copy in flight land before leaving
+      return;
+    }
+    x = xs;
+  }
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= a.n_warps) return;
+  const int64_t r0 = a.warp_row[warp], r1 = a.warp_row[warp + 1];
+  const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
+  const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
+  double acc0 = 0.0, acc1 = 0.0;  // per-lane partials of the epilogue reductions
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int nr = (int)((r1 - base) < 32 ? (r1 - base) : 32);
+    int64_t ms = 0, me = 0;
+    if (lane < nr) {
+      ms = a.rp[base + lane];
+      me = a.rp[base + lane + 1];
+    }
+    Acc myD = 0, myL = 0;
+    unsigned todo = __ballot_sync(kFull, me > ms);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t s = __shfl_sync(kFull, ms, j), e = __shfl_sync(kFull, me, j);
+      Acc dD, dL;
+      row_dot<VT, Acc, S>(a.col, Dv, Lv, s, e, x, lane, dD, dL);
+      if (lane == j) { myD = dD; myL = dL; }
+    }
+    if (lane < nr) {
+      const int64_t r = base + lane;
+      const double sd = a.sD ? (double)a.sD[r] : 1.0;
+      const double sl = a.sL ? (double)a.sL[r] : 1.0;
+      if (EPI == EPI_FINAL) {
+        const double Dx = (double)myD * sd, Lx = (double)myL * sl;
+        a.y64[r] = make_double2(Dx, Lx);
+        const int64_t v = a.voxel ? a.voxel[r] : r;
+        if (a.dose_out) a.dose_out[v] = (float)Dx;
+        if (a.letd_out) a.letd_out[v] = Dx > 0.0 ? (float)(Lx / Dx) : 0.0f;
+      } else {
+        const float Dx = (float)((double)myD * sd), Lx = (float)((double)myL * sl);
+        a.y[r] = make_float2(Dx, Lx);
+        if (EPI == EPI_OBJ) {
+          double f, rD, rL;
+          row_objective(t, a.mask[r], Dx, Lx, f, rD, rL);
+          a.r_out[r] = make_float2((float)(rD * sd), (float)(rL * sl));
+          acc0 += f;
+        } else if (EPI == EPI_BC) {
+          // B' = sum w (q(x) - T) q(g) = 1/2 (rD Dg + rL Lg); C' = sum w q(g)^2
+          const float2 rin = a.r_in[r];  // already multiplied by the row scales
+          acc0 += 0.5 * ((double)rin.x * (double)myD + (double)rin.y * (double)myL);
+          const uint32_t m = a.mask[r];
+          double PD = 0.0, PL = 0.0;
+          for (int i = 0; i < t.n_obj; ++i) {
+            if (!((m >> t.obj[i].bit) & 1u)) continue;
+            if (t.obj[i].q == 0) PD += t.obj[i].weight;
+            else PL += t.obj[i].weight;
+          }
+          acc1 += PD * (double)Dx * (double)Dx + PL * t.c * t.c * (double)Lx * (double)Lx;
+        }
+      }
+    }
+  }
+  if (EPI == EPI_OBJ || EPI == EPI_BC) {
+    acc0 = warp_sum(acc0);
+    acc1 = warp_sum(acc1);
+    if (lane == 0) {
+      a.part[warp] = acc0;
+      if (EPI == EPI_BC) a.part[a.n_warps + warp] = acc1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ K3
+
+template <typename VT, bool S, bool UD>
+__global__ void __launch_bounds__(kBwdThreads) k_backward(BwdArgs a) {
+  constexpr int V = VecOf<VT>::V;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= a.n_warps) return;
+  const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
+  const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
+  const int32_t* __restrict__ row = a.row;
+  const float2* __restrict__ cf = a.coef;
+  const int c1 = a.warp_chunk[warp + 1];
+  for (int c = a.warp_chunk[warp]; c < c1; ++c) {
+    const int64_t s = a.chunk_ptr[c], e = a.chunk_ptr[c + 1];
+    int64_t al = (s + V - 1) & ~(int64_t)(V - 1);
+    if (al > e) al = e;
+    const int64_t ev = al + ((e - al) & ~(int64_t)(V - 1));
+    float acc = 0.0f;
+    {
+      const int64_t p = s + lane;
+      if (p < al) {
+        const float2 g = __ldg(&cf[row[p]]);
+        if (UD) acc = fmaf(to_f(Dv[p]), g.x, acc);
+        acc = fmaf(to_f(Lv[p]), g.y, acc);
+      }
+    }
+    int64_t p = al + (int64_t)lane * V;
+    for (; p + 32 * V < ev; p += 64 * V) {
+      int r0[V], r1[V];
+      float d0[V], d1[V], l0[V], l1[V];
+      load_cols<V, S>(row + p, r0);
+      load_cols<V, S>(row + p + 32 * V, r1);
+      if (UD) {
+        unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
+        unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p + 32 * V)), d1);
+      }
+      unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
+      unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p + 32 * V)), l1);
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const float2 g = __ldg(&cf[r0[q]]);
+        if (UD) acc = fmaf(d0[q], g.x, acc);
+        acc = fmaf(l0[q], g.y, acc);
+      }
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const float2 g = __ldg(&cf[r1[q]]);
+        if (UD) acc = fmaf(d1[q], g.x, acc);
+        acc = fmaf(l1[q], g.y, acc);
+      }
+    }
+    if (p < ev) {
+      int r0[V];
+      float d0[V], l0[V];
+      load_cols<V, S>(row + p, r0);
+      if (UD) unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
+      unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const float2 g = __ldg(&cf[r0[q]]);
+        if (UD) acc = fmaf(d0[q], g.x, acc);
+        acc = fmaf(l0[q], g.y, acc);
+      }
+    }
+    {
+      const int64_t t = ev + lane;
+      if (t < e) {
+        const float2 g = __ldg(&cf[row[t]]);
+        if (UD) acc = fmaf(to_f(Dv[t]), g.x, acc);
+        acc = fmaf(to_f(Lv[t]), g.y, acc);
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) a.chunk_sum[c] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ block reductions
+
+// Fixed-order block reduction of one double per thread (blockDim = 256).
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+__device__ __forceinline__ double block_max256(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+// Sum of n doubles in a fixed order (strided per thread, then the tree).
+__device__ __forceinline__ double block_sum_array(const double* p, int n, double* red) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) v += p[i];
+  return block_sum256(v, red);
+}
+__device__ __forceinline__ double block_max_array(const double* p, int n, double* red) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) v = fmax(v, p[i]);
+  return block_max256(v, red);
+}
+
+// ------------------------------------------------------------------ K3b
+
+template <int MODE>
+__global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
+  __shared__ double red[kColThreads];
+  __shared__ double sh_scale;
+  __shared__ bool sh_last;
+  if (MODE == COL_PROJ) {
+    double W = a.W_all;
+    if (a.norm == 1) W = block_sum_array(a.k2part, a.k2_blocks, red);
+    if (threadIdx.x == 0) {
+      const double ps = a.in_solve ? pow(a.st->eta, (double)a.st->k) : a.prio_scale;
+      sh_scale = W > 0.0 ? a.lam * ps / W : 0.0;
+    }
+    __syncthreads();
+  }
+  const double coef = (MODE == COL_PROJ && a.use_coef) ? a.st->coef : 0.0;
+  const int per = (a.n + gridDim.x - 1) / gridDim.x;
+  const int j0 = blockIdx.x * per, j1 = min(a.n, j0 + per);
+  double acc = 0.0;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    float s = 0.0f;
+    if (a.use_u) {
+      const int c1 = a.col_chunk[j + 1];
+      for (int c = a.col_chunk[j]; c < c1; ++c) s += a.chunk_sum[c];
+    }
+    if (MODE == COL_OUT) {
+      a.out[j] = s;
+    } else if (MODE == COL_GRAD) {
+      a.out[j] = s;
+      acc += (double)s * (double)s;
+    } else {
+      double xj = (double)a.w[j];
+      if (a.use_coef) xj += coef * (double)a.g[j];
+      const double wn = xj + sh_scale * (double)s;
+      a.w[j] = wn > 0.0 ? (float)wn : 0.0f;
+    }
+  }
+  if (MODE == COL_GRAD) {
+    acc = block_sum256(acc, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = acc;
+  }
+  if (MODE == COL_PROJ && a.in_solve) {
+    // the last block to finish closes the iteration: log entry, k <- k + 1
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.st->done, 1u);
+      sh_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (sh_last) {
+      __threadfence();
+      const double nviol = block_sum_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
+      const double mxv = block_max_array(a.k2part + 2 * a.k2_blocks, a.k2_blocks, red);
+      if (threadIdx.x == 0) {
+        DevState* st = a.st;
+        if (st->log_cap > 0) {
+          LogEntry e;
+          e.k = st->k;
+          e.s = st->s;
+          e.accepted = st->accepted;
+          e.n_violated = (int)nviol;
+          e.beta = st->beta_acc;
+          e.f_start = st->f_start;
+          e.f_end = st->f_cur;
+          e.gnorm = st->gnorm;
+          e.max_violation = mxv;
+          a.log[st->k % st->log_cap] = e;
+        }
+        st->k += 1;
+        st->done = 0u;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ K2
+
+__global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t) {
+  __shared__ double red[kRowThreads];
+  const int64_t per = (a.n_hot + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * per;
+  const int64_t i1 = min(a.n_hot, i0 + per);
+  const double coef = a.use_coef ? a.st->coef : 0.0;
+  double psum = 0.0, nv = 0.0, mx = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint32_t m = a.mask[i];
+    float2 out = make_float2(0.f, 0.f);
+    if (m) {
+      const float2 w2 = a.yw[i];
+      double xd = w2.x, xl = w2.y;
+      if (a.use_coef) {
+        const float2 g2 = a.yg[i];
+        xd += coef * (double)g2.x;
+        xl += coef * (double)g2.y;
+      }
+      double gD = 0.0, gL = 0.0;
+      for (int q = 0; q < t.n_con; ++q) {
+        const ConEntry& c = t.con[q];
+        if (!((m >> c.bit) & 1u)) continue;
+        double v, n2, b;
+        const int fam = c.kind >> 1;  // 0 dose, 1 cDL, 2 LETd
+        if (fam == 0) {
+          v = xd; n2 = a.dd[i]; b = c.bound;
+        } else if (fam == 1) {
+          v = t.c * xl; n2 = t.c * t.c * a.ll[i]; b = c.bound;
+        } else {
+          v = xl - c.bound * xd;
+          n2 = a.ll[i] - 2.0 * c.bound * a.dl[i] + c.bound * c.bound * a.dd[i];
+          b = 0.0;
+        }
+        if (!(n2 > 0.0)) continue;  // unreachable row
+        const bool upper = (c.kind & 1) != 0;
+        const double viol = upper ? v - b : b - v;
+        if (viol > 0.0) {
+          const double tt = c.prio * (b - v) / n2;
+          if (fam == 0) gD += tt;
+          else if (fam == 1) gL += t.c * tt;
+          else { gD -= c.bound * tt; gL += tt; }
+          psum += c.prio;
+          nv += 1.0;
+          const double vu = (fam == 2) ? (xd > 0.0 ? viol / xd : 0.0) : viol;  // LETd in keV/um
+          mx = fmax(mx, vu);
+        }
+      }
+      const double sd = a.sD ? (double)a.sD[i] : 1.0;
+      const double sl = a.sL ? (double)a.sL[i] : 1.0;
+      out = make_float2((float)(gD * sd), (float)(gL * sl));
+    }
+    a.gam[i] = out;
+  }
+  psum = block_sum256(psum, red);
+  nv = block_sum256(nv, red);
+  mx = block_max256(mx, red);
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x] = psum;
+    a.part[gridDim.x + blockIdx.x] = nv;
+    a.part[2 * gridDim.x + blockIdx.x] = mx;
+  }
+}
+
+// ------------------------------------------------------------------ K4
+
+__global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, int nf,
+                                                const double* part_bc, int nbc, const double* part_g,
+                                                int ng, DevState* st) {
+  __shared__ double red[256];
+  const double f = block_sum_array(part_f, nf, red);
+  const double Bp = block_sum_array(part_bc, nbc, red);
+  const double Cp = block_sum_array(part_bc + nbc, nbc, red);
+  const double gn2 = block_sum_array(part_g, ng, red);
+  if (threadIdx.x != 0) return;
+  if (step == 0) {
+    st->f_start = f;
+    st->accepted = 0;
+    st->beta_acc = 0.0;
+  }
+  double fc = f;
+  double coef = 0.0;
+  long long s = st->s;
+  if (gn2 > 0.0) {
+    const double gn = sqrt(gn2);
+    st->gnorm = gn;
+    double B, C;
+    if (st->grad_normalize) { B = -Bp / gn; C = Cp / gn2; }
+    else { B = -Bp; C = Cp; }
+    for (int tr = 0; tr < st->max_trials; ++tr) {
+      const double beta = st->beta0 * pow(st->alpha, (double)s);
+      s += 1;
+      const double df = beta * (2.0 * B + beta * C);  // f(x + beta v) - f(x), Eq. 2 is quadratic
+      if (df <= 0.0) {
+        coef = st->grad_normalize ? -beta / gn : -beta;
+        st->accepted += 1;
+        st->accepted_total += 1;
+        st->beta_acc = beta;
+        fc = f + df;
+        break;
+      }
+    }
+  } else {
+    st->gnorm = 0.0;
+  }
+  st->s = s;
+  st->coef = coef;
+  st->f_cur = fc;
+}
+
+// x <- x + coef g for the next perturbation step (reductions > 1)
+__global__ void k_apply_step(int64_t n_hot, int n, float* w, const float* g, float2* yw,
+                             const float2* yg, const DevState* st) {
+  const double coef = st->coef;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = (float)((double)w[i] + coef * (double)g[i]);
+  if (i < n_hot) {
+    const float2 a = yw[i], b = yg[i];
+    yw[i] = make_float2((float)((double)a.x + coef * b.x), (float)((double)a.y + coef * b.y));
+  }
+}
+
+__global__ void __launch_bounds__(kRowThreads) k_row_objective(Tables t, const float2* yw,
+                                                              const uint32_t* mask, const float* sD,
+                                                              const float* sL, int64_t n_hot,
+                                                              float2* r_out, double* part) {
+  __shared__ double red[kRowThreads];
+  const int64_t per = (n_hot + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n_hot, i0 + per);
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const float2 y = yw[i];
+    double f, rD, rL;
+    row_objective(t, mask[i], y.x, y.y, f, rD, rL);
+    const double sd = sD ? (double)sD[i] : 1.0, sl = sL ? (double)sL[i] : 1.0;
+    r_out[i] = make_float2((float)(rD * sd), (float)(rL * sl));
+    acc += f;
+  }
+  acc = block_sum256(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// FP64 check at the final point: per block [max violation per kind (6), n violated, f]
+__global__ void __launch_bounds__(kRowThreads) k_final_check(Tables t, const double2* y64,
+                                                            const uint32_t* mask, const double* dd,
+                                                            const double* ll, const double* dl,
+                                                            int64_t n_hot, double* part) {
+  __shared__ double red[kRowThreads];
+  const int64_t per = (n_hot + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n_hot, i0 + per);
+  double mk[6] = {0, 0, 0, 0, 0, 0};
+  double nv = 0.0, fo = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint32_t m = mask[i];
+    if (!m) continue;
+    const double2 y = y64[i];
+    for (int q = 0; q < t.n_con; ++q) {
+      const ConEntry& c = t.con[q];
+      if (!((m >> c.bit) & 1u)) continue;
+      const int fam = c.kind >> 1;
+      double v, n2, b;
+      if (fam == 0) { v = y.x; n2 = dd[i]; b = c.bound; }
+      else if (fam == 1) { v = t.c * y.y; n2 = ll[i]; b = c.bound; }
+      else {
+        v = y.y - c.bound * y.x;
+        n2 = ll[i] - 2.0 * c.bound * dl[i] + c.bound * c.bound * dd[i];
+        b = 0.0;
+      }
+      if (!(n2 > 0.0)) continue;
+      const double viol = (c.kind & 1) ? v - b : b - v;
+      if (viol > 0.0) {
+        nv += 1.0;
+        const double vu = (fam == 2) ? (y.x > 0.0 ? viol / y.x : 0.0) : viol;
+        mk[c.kind] = fmax(mk[c.kind], vu);
+      }
+    }
+    double f, rD, rL;
+    row_objective(t, m, y.x, y.y, f, rD, rL);
+    fo += f;
+  }
+  for (int q = 0; q < 6; ++q) {
+    const double v = block_max256(mk[q], red);
+    if (threadIdx.x == 0) part[blockIdx.x * 8 + q] = v;
+  }
+  nv = block_sum256(nv, red);
+  fo = block_sum256(fo, red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x * 8 + 6] = nv;
+    part[blockIdx.x * 8 + 7] = fo;
+  }
+}
+
+__global__ void k_begin_state(DevState* st) {
+  st->k = 0;
+  st->s = 0;
+  st->accepted_total = 0;
+  st->accepted = 0;
+  st->coef = 0.0;
+  st->f_start = st->f_cur = st->gnorm = st->beta_acc = 0.0;
+  st->err = 0;
+  st->done = 0u;
+}
+
+// ------------------------------------------------------------------ K5 setup
+
+__global__ void k_validate(const int64_t* rp, const int32_t* col, const float* D, const float* L,
+                           int64_t n_rows, int32_t n_cols, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += nw) {
+    const int64_t s = rp[r], e = rp[r + 1];
+    int bad = 0;
+    for (int64_t p = s + lane; p < e; p += 32) {
+      const int c = col[p];
+      if (c < 0 || c >= n_cols) bad |= 1;
+      if (p > s && col[p - 1] >= c) bad |= 1;
+      if (!isfinite(D[p]) || !isfinite(L[p])) bad |= 2;
+    }
+    bad = __reduce_or_sync(kFull, bad);
+    if (bad && lane == 0) atomicOr(err, bad);
+  }
+}
+
+__global__ void k_gather_rows(const int64_t* rp_src, const int64_t* src_row, const int64_t* rp_dst,
+                              int64_t n_rows, const int32_t* col_src, const float* D_src,
+                              const float* L_src, int32_t* col_dst, float* D_dst, float* L_dst) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += nw) {
+    const int64_t sr = src_row[r];
+    const int64_t s = rp_src[sr], e = rp_src[sr + 1], d = rp_dst[r];
+    for (int64_t p = s + lane; p < e; p += 32) {
+      col_dst[d + (p - s)] = col_src[p];
+      D_dst[d + (p - s)] = D_src[p];
+      L_dst[d + (p - s)] = L_src[p];
+    }
+  }
+}
+
+// Power-of-two scale so that scale * q is exact in binary32:
+// BF16: max|q| in (1/2, 1]; FP16: max|q| in (2^13, 2^14] (all normal values
+// down to 2^-28 of the row maximum keep 11 significant bits).
+__device__ __forceinline__ float pow2_scale(float amax, int fmt) {
+  if (!(amax > 0.0f)) return 1.0f;
+  int ex;
+  frexpf(amax, &ex);  // amax in [2^(ex-1), 2^ex)
+  return ldexpf(1.0f, fmt == 2 ? ex - 14 : ex);
+}
+
+template <typename VT>
+__device__ __forceinline__ VT from_f(float v);
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+
+template <typename VT>
+__global__ void k_quantize(int fmt, const int64_t* rp, int64_t n_rows, const float* D, const float* L,
+                           VT* qD, VT* qL, float* sD, float* sL) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += nw) {
+    const int64_t s = rp[r], e = rp[r + 1];
+    float mD = 0.f, mL = 0.f;
+    for (int64_t p = s + lane; p < e; p += 32) {
+      mD = fmaxf(mD, fabsf(D[p]));
+      mL = fmaxf(mL, fabsf(L[p]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mD = fmaxf(mD, __shfl_xor_sync(kFull, mD, o));
+      mL = fmaxf(mL, __shfl_xor_sync(kFull, mL, o));
+    }
+    const float scD = pow2_scale(mD, fmt), scL = pow2_scale(mL, fmt);
+    for (int64_t p = s + lane; p < e; p += 32) {
+      qD[p] = from_f<VT>(D[p] / scD);
+      qL[p] = from_f<VT>(L[p] / scL);
+    }
+    if (lane == 0) { sD[r] = scD; sL[r] = scL; }
+  }
+}
+
+template <typename VT>
+__global__ void k_moments(const int64_t* rp, int64_t n_rows, const VT* Dv, const VT* Lv,
+                          const float* sD, const float* sL, double* dd, double* ll, double* dl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += nw) {
+    const int64_t s = rp[r], e = rp[r + 1];
+    const double sd = sD ? (double)sD[r] : 1.0, sl = sL ? (double)sL[r] : 1.0;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int64_t p = s + lane; p < e; p += 32) {
+      const double d = sd * (double)to_f(Dv[p]);
+      const double l = sl * (double)to_f(Lv[p]);
+      a += d * d;
+      b += l * l;
+      c += d * l;
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    if (lane == 0) { dd[r] = a; ll[r] = b; dl[r] = c; }
+  }
+}
+
+// blocked counting transpose: block b owns rows [blk_row[b], blk_row[b+1])
+__global__ void k_csc_count(const int64_t* rp, const int32_t* col, const int64_t* blk_row,
+                            int32_t n_cols, int32_t* cnt) {
+  const int b = blockIdx.x;
+  const int64_t s = rp[blk_row[b]], e = rp[blk_row[b + 1]];
+  int32_t* c = cnt + (int64_t)b * n_cols;
+  for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) atomicAdd(&c[col[p]], 1);
+}
+
+__global__ void k_csc_colsum(const int32_t* cnt, int n_blk, int32_t n_cols, int64_t* tot) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_cols) return;
+  int64_t s = 0;
+  for (int b = 0; b < n_blk; ++b) s += cnt[(int64_t)b * n_cols + j];
+  tot[j] = s;
+}
+
+// cnt[b][j] <- first output position of block b's entries of column j
+__global__ void k_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int64_t* cp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_cols) return;
+  int64_t run = cp[j];
+  for (int b = 0; b < n_blk; ++b) {
+    const int64_t i = (int64_t)b * n_cols + j;
+    const int32_t t = cnt[i];
+    cnt[i] = (int32_t)run;  // positions < 2^31 (checked on the host)
+    run += t;
+  }
+}
+
+// Rows of a block in ascending order; within a row all columns differ, so
+// the cursor updates of one row never collide; a barrier separates rows,
+// which keeps the rows of every column ascending (a stable transpose).
+template <typename VT>
+__global__ void k_csc_fill(const int64_t* rp, const int32_t* col, const VT* Dv, const VT* Lv,
+                           const int64_t* blk_row, int32_t n_cols, int32_t* cursor, int32_t* row_out,
+                           VT* DT, VT* LT) {
+  const int b = blockIdx.x;
+  int32_t* cur = cursor + (int64_t)b * n_cols;
+  for (int64_t r = blk_row[b]; r < blk_row[b + 1]; ++r) {
+    const int64_t s = rp[r], e = rp[r + 1];
+    for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) {
+      const int c = col[p];
+      const int32_t pos = cur[c];
+      cur[c] = pos + 1;
+      row_out[pos] = (int32_t)r;
+      DT[pos] = Dv[p];
+      LT[pos] = Lv[p];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename VT>
+__global__ void k_dequant_csc(const int64_t* cp, int32_t n_cols, const int32_t* row, const VT* DT,
+                              const VT* LT, const float* sD, const float* sL, float* Dout, float* Lout) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n_cols; j += nw) {
+    for (int64_t p = cp[j] + lane; p < cp[j + 1]; p += 32) {
+      const int r = row[p];
+      Dout[p] = (sD ? sD[r] : 1.0f) * to_f(DT[p]);
+      Lout[p] = (sL ? sL[r] : 1.0f) * to_f(LT[p]);
+    }
+  }
+}
+
+__global__ void k_scale_coef(int64_t n, const float* aD, const float* aL, const int64_t* voxel,
+                             const float* sD, const float* sL, float2* coef) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t v = voxel ? voxel[i] : i;
+  const float d = aD ? aD[v] : 0.0f, l = aL ? aL[v] : 0.0f;
+  coef[i] = make_float2(sD ? d * sD[i] : d, sL ? l * sL[i] : l);
+}
+
+
+// reachable constraint rows (|a_r|^2 > 0): per block [count, unreachable, sum of priorities]
+__global__ void __launch_bounds__(kRowThreads) k_count_rows(Tables t, const uint32_t* mask,
+                                                           const double* dd, const double* ll,
+                                                           const double* dl, int64_t n_hot,
+                                                           double* part) {
+  __shared__ double red[kRowThreads];
+  const int64_t per = (n_hot + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n_hot, i0 + per);
+  double nr = 0.0, nu = 0.0, W = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint32_t m = mask[i];
+    if (!m) continue;
+    for (int q = 0; q < t.n_con; ++q) {
+      const ConEntry& c = t.con[q];
+      if (!((m >> c.bit) & 1u)) continue;
+      const int fam = c.kind >> 1;
+      const double n2 = fam == 0 ? dd[i]
+                      : fam == 1 ? ll[i]
+                                 : ll[i] - 2.0 * c.bound * dl[i] + c.bound * c.bound * dd[i];
+      if (n2 > 0.0) { nr += 1.0; W += c.prio; }
+      else nu += 1.0;
+    }
+  }
+  nr = block_sum256(nr, red);
+  nu = block_sum256(nu, red);
+  W = block_sum256(W, red);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = nr;
+    part[3 * blockIdx.x + 1] = nu;
+    part[3 * blockIdx.x + 2] = W;
+  }
+}
+
+__global__ void k_scatter_y(const float2* y, const int64_t* voxel, int64_t n, float* a, float* b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t v = voxel ? voxel[i] : i;
+  const float2 t = y[i];
+  if (a) a[v] = t.x;
+  if (b) b[v] = t.y;
+}
+
+// ------------------------------------------------------------------ launch wrappers
+
+template <typename VT, int EPI, bool XS, bool S>
+static void fwd_inst(const Geometry& g, const FwdArgs& a, const Tables& t, cudaStream_t s) {
+  const size_t smem = XS ? (size_t)a.n_x_pad * sizeof(float) + 16 : 0;
+  k_forward<VT, EPI, XS, S><<<g.fwd_blocks, g.fwd_threads, smem, s>>>(a, t);
+}
+
+template <typename VT, int EPI>
+static void fwd_dispatch_xs(const Geometry& g, bool xs, bool st, const FwdArgs& a, const Tables& t,
+                            cudaStream_t s) {
+  if (EPI == EPI_FINAL) {
+    if (xs) fwd_inst<VT, EPI, true, false>(g, a, t, s);
+    else fwd_inst<VT, EPI, false, false>(g, a, t, s);
+    return;
+  }
+  if (xs) {
+    if (st) fwd_inst<VT, EPI, true, true>(g, a, t, s);
+    else fwd_inst<VT, EPI, true, false>(g, a, t, s);
+  } else {
+    if (st) fwd_inst<VT, EPI, false, true>(g, a, t, s);
+    else fwd_inst<VT, EPI, false, false>(g, a, t, s);
+  }
+}
+
+template <typename VT>
+static void fwd_dispatch_epi(const Geometry& g, int epi, bool xs, bool st, const FwdArgs& a,
+                             const Tables& t, cudaStream_t s) {
+  switch (epi) {
+    case EPI_STORE: fwd_dispatch_xs<VT, EPI_STORE>(g, xs, st, a, t, s); break;
+    case EPI_OBJ: fwd_dispatch_xs<VT, EPI_OBJ>(g, xs, st, a, t, s); break;
+    case EPI_BC: fwd_dispatch_xs<VT, EPI_BC>(g, xs, st, a, t, s); break;
+    default: fwd_dispatch_xs<VT, EPI_FINAL>(g, xs, st, a, t, s); break;
+  }
+}
+
+bool forward_uses_smem(const Geometry& g, int n_x_pad) {
+  return (size_t)n_x_pad * sizeof(float) + 16 <= g.smem_limit;
+}
+
+void launch_forward(const Geometry& g, int fmt, int epi, bool stream_hint, const FwdArgs& a,
+                    const Tables& t, cudaStream_t s) {
+  const bool xs = forward_uses_smem(g, a.n_x_pad);
+  if (fmt == 1) fwd_dispatch_epi<__nv_bfloat16>(g, epi, xs, stream_hint, a, t, s);
+  else if (fmt == 2) fwd_dispatch_epi<__half>(g, epi, xs, stream_hint, a, t, s);
+  else fwd_dispatch_epi<float>(g, epi, xs, stream_hint, a, t, s);
+}
+
+template <typename VT>
+static void bwd_dispatch(const Geometry& g, bool st, bool ud, const BwdArgs& a, cudaStream_t s) {
+  if (st) {
+    if (ud) k_backward<VT, true, true><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+    else k_backward<VT, true, false><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+  } else {
+    if (ud) k_backward<VT, false, true><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+    else k_backward<VT, false, false><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+  }
+}
+
+void launch_backward(const Geometry& g, int fmt, bool stream_hint, bool use_D, const BwdArgs& a,
+                     cudaStream_t s) {
+  if (fmt == 1) bwd_dispatch<__nv_bfloat16>(g, stream_hint, use_D, a, s);
+  else if (fmt == 2) bwd_dispatch<__half>(g, stream_hint, use_D, a, s);
+  else bwd_dispatch<float>(g, stream_hint, use_D, a, s);
+}
+
+void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_t s) {
+  if (mode == COL_OUT) k_colfinish<COL_OUT><<<g.col_blocks, kColThreads, 0, s>>>(a);
+  else if (mode == COL_GRAD) k_colfinish<COL_GRAD><<<g.col_blocks, kColThreads, 0, s>>>(a);
+  else k_colfinish<COL_PROJ><<<g.col_blocks, kColThreads, 0, s>>>(a);
+}
+
+void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s) {
+  k_constraints<<<g.row_blocks, kRowThreads, 0, s>>>(a, t);
+}
+
+void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
+                   const double* part_g, int ng, DevState* st, cudaStream_t s) {
+  k_finish<<<1, 256, 0, s>>>(step, part_f, nf, part_bc, nbc, part_g, ng, st);
+}
+
+void launch_apply_step(int64_t n_hot, int n, float* w, const float* g, float2* yw, const float2* yg,
+                       const DevState* st, cudaStream_t s) {
+  const int64_t m = n_hot > n ? n_hot : n;
+  if (m == 0) return;
+  k_apply_step<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n_hot, n, w, g, yw, yg, st);
+}
+
+void launch_row_objective(const Geometry& g, const Tables& t, const float2* yw, const uint32_t* mask,
+                          const float* sD, const float* sL, int64_t n_hot, float2* r_out,
+                          double* part, cudaStream_t s) {
+  k_row_objective<<<g.row_blocks, kRowThreads, 0, s>>>(t, yw, mask, sD, sL, n_hot, r_out, part);
+}
+
+void launch_final_check(const Geometry& g, const Tables& t, const double2* y64, const uint32_t* mask,
+                        const double* dd, const double* ll, const double* dl, int64_t n_hot,
+                        double* part, cudaStream_t s) {
+  k_final_check<<<g.row_blocks, kRowThreads, 0, s>>>(t, y64, mask, dd, ll, dl, n_hot, part);
+}
+
+void launch_begin_state(DevState* st, cudaStream_t s) { k_begin_state<<<1, 1, 0, s>>>(st); }
+
+void launch_count_rows(const Geometry& g, const Tables& t, const uint32_t* mask, const double* dd,
+                       const double* ll, const double* dl, int64_t n_hot, double* part,
+                       cudaStream_t s) {
+  k_count_rows<<<g.row_blocks, kRowThreads, 0, s>>>(t, mask, dd, ll, dl, n_hot, part);
+}
+
+void launch_scatter_y(const float2* y, const int64_t* voxel, int64_t n, float* a, float* b,
+                      cudaStream_t s) {
+  if (n == 0) return;
+  k_scatter_y<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, voxel, n, a, b);
+}
+
+static unsigned grid_for(int64_t work, int per_block, int cap) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+void launch_validate(const int64_t* rp, const int32_t* col, const float* D, const float* L,
+                     int64_t n_rows, int32_t n_cols, int64_t, int* err, cudaStream_t s) {
+  if (n_rows == 0) return;
+  k_validate<<<grid_for(n_rows, 8, 65535), 256, 0, s>>>(rp, col, D, L, n_rows, n_cols, err);
+}
+
+void launch_gather_rows(const int64_t* rp_src, const int64_t* src_row, const int64_t* rp_dst,
+                        int64_t n_rows, const int32_t* col_src, const float* D_src,
+                        const float* L_src, int32_t* col_dst, float* D_dst, float* L_dst,
+                        cudaStream_t s) {
+  if (n_rows == 0) return;
+  k_gather_rows<<<grid_for(n_rows, 8, 65535), 256, 0, s>>>(rp_src, src_row, rp_dst, n_rows, col_src,
+                                                          D_src, L_src, col_dst, D_dst, L_dst);
+}
+
+void launch_quantize(int fmt, const int64_t* rp, int64_t n_rows, const float* D, const float* L,
+                     void* qD, void* qL, float* sD, float* sL, cudaStream_t s) {
+  if (n_rows == 0) return;
+  const unsigned gb = grid_for(n_rows, 8, 65535);
+  if (fmt == 1)
+    k_quantize<__nv_bfloat16><<<gb, 256, 0, s>>>(fmt, rp, n_rows, D, L, (__nv_bfloat16*)qD,
+                                                  (__nv_bfloat16*)qL, sD, sL);
+  else
+    k_quantize<__half><<<gb, 256, 0, s>>>(fmt, rp, n_rows, D, L, (__half*)qD, (__half*)qL, sD, sL);
+}
+
+void launch_moments(int fmt, const int64_t* rp, int64_t n_rows, const void* Dv, const void* Lv,
+                    const float* sD, const float* sL, double* dd, double* ll, double* dl,
+                    cudaStream_t s) {
+  if (n_rows == 0) return;
+  const unsigned gb = grid_for(n_rows, 8, 65535);
+  if (fmt == 1)
+    k_moments<__nv_bfloat16><<<gb, 256, 0, s>>>(rp, n_rows, (const __nv_bfloat16*)Dv,
+                                                 (const __nv_bfloat16*)Lv, sD, sL, dd, ll, dl);
+  else if (fmt == 2)
+    k_moments<__half><<<gb, 256, 0, s>>>(rp, n_rows, (const __half*)Dv, (const __half*)Lv, sD, sL, dd,
+                                          ll, dl);
+  else
+    k_moments<float><<<gb, 256, 0, s>>>(rp, n_rows, (const float*)Dv, (const float*)Lv, sD, sL, dd,
+                                         ll, dl);
+}
+
+void launch_csc_count(const int64_t* rp, const int32_t* col, const int64_t* blk_row, int n_blk,
+                      int32_t n_cols, int32_t* cnt, cudaStream_t s) {
+  k_csc_count<<<n_blk, 256, 0, s>>>(rp, col, blk_row, n_cols, cnt);
+}
+
+void launch_csc_colsum(const int32_t* cnt, int n_blk, int32_t n_cols, int64_t* tot, cudaStream_t s) {
+  k_csc_colsum<<<(n_cols + 255) / 256, 256, 0, s>>>(cnt, n_blk, n_cols, tot);
+}
+
+void launch_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int64_t* cp, cudaStream_t s) {
+  k_csc_offsets<<<(n_cols + 255) / 256, 256, 0, s>>>(cnt, n_blk, n_cols, cp);
+}
+
+void launch_csc_fill(int fmt, const int64_t* rp, const int32_t* col, const void* Dv, const void* Lv,
+                     const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor,
+                     int32_t* row_out, void* DT, void* LT, cudaStream_t s) {
+  if (fmt == 0)
+    k_csc_fill<float><<<n_blk, 256, 0, s>>>(rp, col, (const float*)Dv, (const float*)Lv, blk_row,
+                                            n_cols, cursor, row_out, (float*)DT, (float*)LT);
+  else
+    k_csc_fill<uint16_t><<<n_blk, 256, 0, s>>>(rp, col, (const uint16_t*)Dv, (const uint16_t*)Lv,
+                                               blk_row, n_cols, cursor, row_out, (uint16_t*)DT,
+                                               (uint16_t*)LT);
+}
+
+void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_t* row, const void* DT,
+                        const void* LT, const float* sD, const float* sL, float* Dout, float* Lout,
+                        cudaStream_t s) {
+  const unsigned gb = grid_for(n_cols, 8, 65535);
+  if (fmt == 1)
+    k_dequant_csc<__nv_bfloat16><<<gb, 256, 0, s>>>(cp, n_cols, row, (const __nv_bfloat16*)DT,
+                                                     (const __nv_bfloat16*)LT, sD, sL, Dout, Lout);
+  else if (fmt == 2)
+    k_dequant_csc<__half><<<gb, 256, 0, s>>>(cp, n_cols, row, (const __half*)DT, (const __half*)LT, sD,
+                                              sL, Dout, Lout);
+  else
+    k_dequant_csc<float><<<gb, 256, 0, s>>>(cp, n_cols, row, (const float*)DT, (const float*)LT, sD,
+                                             sL, Dout, Lout);
+}
+
+void launch_scale_coef(int64_t n, const float* aD, const float* aL, const int64_t* voxel,
+                       const float* sD, const float* sL, float2* coef, cudaStream_t s) {
+  if (n == 0) return;
+  k_scale_coef<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, aD, aL, voxel, sD, sL, coef);
+}
+
+// ------------------------------------------------------------------ init
+
+template <typename VT, int EPI>
+static cudaError_t set_smem_attr(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_forward<VT, EPI, true, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  if (EPI != EPI_FINAL)
+    e = cudaFuncSetAttribute(k_forward<VT, EPI, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+template <typename VT>
+static cudaError_t set_smem_all(int bytes) {
+  cudaError_t e;
+  if ((e = set_smem_attr<VT, EPI_STORE>(bytes)) != cudaSuccess) return e;
+  if ((e = set_smem_attr<VT, EPI_OBJ>(bytes)) != cudaSuccess) return e;
+  if ((e = set_smem_attr<VT, EPI_BC>(bytes)) != cudaSuccess) return e;
+  return set_smem_attr<VT, EPI_FINAL>(bytes);
+}
+
+int init_kernels(Geometry* g, int device) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return -1;
+  g->n_sms = prop.multiProcessorCount;
+  g->smem_limit = prop.sharedMemPerBlockOptin;
+  g->fwd_threads = kFwdThreads;
+  g->fwd_blocks = g->n_sms;
+  g->fwd_warps = g->fwd_blocks * (kFwdThreads / 32);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<float, true, true>, kBwdThreads, 0);
+  if (occ < 1) occ = 1;
+  g->bwd_threads = kBwdThreads;
+  g->bwd_blocks = g->n_sms * occ;
+  g->bwd_warps = g->bwd_blocks * (kBwdThreads / 32);
+  g->row_threads = kRowThreads;
+  g->row_blocks = g->n_sms * 4;
+  g->col_threads = kColThreads;
+  g->col_blocks = g->n_sms * 2;
+  const int bytes = (int)g->smem_limit;
+  if (set_smem_all<float>(bytes) != cudaSuccess) return -2;
+  if (set_smem_all<__nv_bfloat16>(bytes) != cudaSuccess) return -2;
+  if (set_smem_all<__half>(bytes) != cudaSuccess) return -2;
+  return 0;
+}
+
+}  // namespace fo

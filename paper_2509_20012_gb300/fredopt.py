@@ -1,0 +1,384 @@
+"""Thin ctypes binding of libfredopt (include/fredopt.h): argument
+marshalling only.  Every step of the method runs in the library's CUDA
+kernels; nothing here computes.
+
+Arrays may be numpy arrays (host) or torch tensors; CUDA tensors are passed
+as device pointers (FREDOPT_DEVICE_PTR), everything else as host memory.
+If libfredopt.so is missing the import fails loudly: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfredopt.so")
+
+# ---- constants (values of include/fredopt.h) ----
+OK = 0
+DEVICE_PTR = 0x1
+FORMATS = {"fp32": 0, "bf16": 1, "fp16": 2}
+ROWS = {"all": 0x000, "roi": 0x100}
+KINDS = {"DOSE_MIN": 0, "DOSE_MAX": 1, "CDL_MIN": 2, "CDL_MAX": 3, "LETD_MIN": 4, "LETD_MAX": 5}
+QUANTITIES = {"DOSE": 0, "CDL": 1}
+NORMS = {"all": 0, "violated": 1}
+KCLASS_N = 6
+KCLASS_NAMES = ["forward", "backward", "constraints", "colfinish", "finish", "other"]
+
+
+class FredoptError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fredopt error {code}: {msg}")
+        self.code = code
+
+
+class Constraint(ctypes.Structure):
+    _fields_ = [("struct_bit", ctypes.c_uint32), ("kind", ctypes.c_int32),
+                ("bound", ctypes.c_double), ("priority", ctypes.c_double)]
+
+
+class ObjectiveTerm(ctypes.Structure):
+    _fields_ = [("struct_bit", ctypes.c_uint32), ("quantity", ctypes.c_int32),
+                ("target", ctypes.c_double), ("weight", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beta0", ctypes.c_double), ("eta", ctypes.c_double),
+                ("reductions", ctypes.c_int32), ("max_trials", ctypes.c_int32),
+                ("cimmino_norm", ctypes.c_int32), ("grad_normalize", ctypes.c_int32),
+                ("c_cdl", ctypes.c_double), ("log_capacity", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32)]
+
+
+class LogEntry(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("s", ctypes.c_int64), ("accepted", ctypes.c_int32),
+                ("n_violated", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("f_start", ctypes.c_double), ("f_end", ctypes.c_double),
+                ("gnorm", ctypes.c_double), ("max_violation", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("s", ctypes.c_int64), ("accepted", ctypes.c_int64),
+                ("n_rows", ctypes.c_int64), ("unreachable_rows", ctypes.c_int64),
+                ("n_violated", ctypes.c_int64), ("objective", ctypes.c_double),
+                ("max_violation", ctypes.c_double * 6), ("beta0", ctypes.c_double),
+                ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["max_violation"] = list(self.max_violation)
+        return d
+
+
+_lib = None
+
+_SIGS = {
+    "fredopt_default_params": (None, [ctypes.POINTER(Params)]),
+    "fredopt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "fredopt_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fredopt_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]),
+    "fredopt_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fredopt_load_influence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]),
+    "fredopt_set_constraints": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Constraint)]),
+    "fredopt_set_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ObjectiveTerm)]),
+    "fredopt_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(Params), ctypes.c_uint32]),
+    "fredopt_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "fredopt_end": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(Report), ctypes.c_uint32]),
+    "fredopt_superiorize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.POINTER(Params), ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Report),
+                                           ctypes.c_uint32]),
+    "fredopt_get_log": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LogEntry), ctypes.c_int]),
+    "fredopt_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32]),
+    "fredopt_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_uint32]),
+    "fredopt_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_uint32]),
+    "fredopt_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_uint32]),
+    "fredopt_feasibility_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32]),
+    "fredopt_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_void_p, ctypes.c_uint32]),
+    "fredopt_get_sizes": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 5),
+    "fredopt_get_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fredopt_get_csc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "fredopt_get_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fredopt_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "fredopt_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fredopt_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfredopt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libfredopt.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load_library().fredopt_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "cimmino_norm" and isinstance(v, str):
+            v = NORMS[v]
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _on_device(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) of a contiguous array of the given numpy dtype."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        tdt = {np.float32: torch.float32, np.int64: torch.int64, np.int32: torch.int32,
+               np.uint32: torch.int32, np.float64: torch.float64}[dtype]
+        if x.dtype != tdt and not (dtype is np.uint32 and x.dtype in (torch.int32, torch.uint32)):
+            raise TypeError(f"expected {tdt}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if not x.is_cuda:
+            return x.data_ptr(), x
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+class Handle:
+    """One plan on one GPU (a fredopt_t)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = self.lib.fredopt_create(ctypes.byref(h), device, s)
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+        self.h = h
+        self.device = device
+        self.n_vox = self.n_spots = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fredopt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc < 0:
+            msg = self.lib.fredopt_last_error(self.h)
+            raise FredoptError(rc, f"{self.lib.fredopt_strerror(rc).decode()}: {msg.decode() if msg else ''}")
+        return rc
+
+    # ---------------------------------------------------------- plan
+    def load_influence(self, row_ptr, col, D, L, mask, n_spots, fmt="fp32", rows="all"):
+        dev = _on_device(row_ptr)
+        n_vox = int(row_ptr.shape[0]) - 1
+        nnz = int(col.shape[0])
+        p_rp, k1 = _ptr(row_ptr, np.int64)
+        p_c, k2 = _ptr(col, np.int32)
+        p_d, k3 = _ptr(D, np.float32)
+        p_l, k4 = _ptr(L, np.float32)
+        p_m, k5 = _ptr(mask, np.uint32)
+        code = FORMATS[fmt] | ROWS[rows]
+        self._check(self.lib.fredopt_load_influence(self.h, n_vox, int(n_spots), nnz, p_rp, p_c, p_d, p_l,
+                                                    p_m, code, DEVICE_PTR if dev else 0))
+        self.n_vox, self.n_spots = n_vox, int(n_spots)
+
+    def set_constraints(self, constraints):
+        arr = (Constraint * max(1, len(constraints)))()
+        for i, c in enumerate(constraints):
+            arr[i] = Constraint(int(c["struct_bit"]), KINDS[c["kind"]], float(c["bound"]), float(c["priority"]))
+        self._check(self.lib.fredopt_set_constraints(self.h, len(constraints), arr))
+
+    def set_objective(self, terms):
+        arr = (ObjectiveTerm * max(1, len(terms)))()
+        for i, t in enumerate(terms):
+            arr[i] = ObjectiveTerm(int(t["struct_bit"]), QUANTITIES[t["quantity"]], float(t["target"]),
+                                   float(t["weight"]))
+        self._check(self.lib.fredopt_set_objective(self.h, len(terms), arr))
+
+    def load_plan(self, plan, fmt="fp32", rows="all"):
+        """Load a phantom.Plan-like object (row_ptr, col, D, L, mask, constraints, objective)."""
+        self.load_influence(plan.row_ptr, plan.col, plan.D, plan.L, plan.mask, plan.n_spots, fmt=fmt, rows=rows)
+        self.set_constraints(plan.constraints)
+        self.set_objective(plan.objective)
+
+    def sizes(self):
+        v = [ctypes.c_int64() for _ in range(5)]
+        self._check(self.lib.fredopt_get_sizes(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(["n_vox", "n_spots", "nnz", "n_rows", "nnz_rows"], [x.value for x in v]))
+
+    # ---------------------------------------------------------- outputs
+    def _out(self, like_dev, n, dtype=np.float32):
+        if like_dev:
+            import torch
+            return torch.empty(n, dtype=torch.float32, device=f"cuda:{self.device}")
+        return np.empty(n, dtype)
+
+    # ---------------------------------------------------------- solve
+    def begin(self, w0, alpha, relaxation, params: Params | None = None, **kw):
+        if params is None:
+            params = default_params(**kw)
+        dev = _on_device(w0)
+        p, keep = _ptr(w0, np.float32)
+        self._check(self.lib.fredopt_begin(self.h, p, float(alpha), float(relaxation), ctypes.byref(params),
+                                           DEVICE_PTR if dev else 0))
+        self._dev = dev
+
+    def iterate(self, iters: int):
+        self._check(self.lib.fredopt_iterate(self.h, int(iters)))
+
+    def end(self, outputs=None):
+        """Returns (w, dose, letd, report dict); outputs=(w, dose, letd) to fill."""
+        dev = getattr(self, "_dev", False)
+        if outputs is None:
+            outputs = (self._out(dev, self.n_spots), self._out(dev, self.n_vox), self._out(dev, self.n_vox))
+        w, d, l = outputs
+        dev = _on_device(w)
+        rep = Report()
+        self._check(self.lib.fredopt_end(self.h, _ptr(w, np.float32)[0], _ptr(d, np.float32)[0] if d is not None else None,
+                                         _ptr(l, np.float32)[0] if l is not None else None, ctypes.byref(rep),
+                                         DEVICE_PTR if dev else 0))
+        return w, d, l, rep.as_dict()
+
+    def superiorize(self, w0, iters, alpha, relaxation, params: Params | None = None, outputs=None, **kw):
+        """One call: begin + iterate + end (fredopt_superiorize)."""
+        if params is None:
+            params = default_params(**kw)
+        dev = _on_device(w0)
+        if outputs is None:
+            outputs = (self._out(dev, self.n_spots), self._out(dev, self.n_vox), self._out(dev, self.n_vox))
+        w, d, l = outputs
+        rep = Report()
+        p0, keep = _ptr(w0, np.float32)
+        self._check(self.lib.fredopt_superiorize(self.h, p0, int(iters), float(alpha), float(relaxation),
+                                                 ctypes.byref(params), _ptr(w, np.float32)[0],
+                                                 _ptr(d, np.float32)[0], _ptr(l, np.float32)[0],
+                                                 ctypes.byref(rep), DEVICE_PTR if dev else 0))
+        self._dev = dev
+        return w, d, l, rep.as_dict()
+
+    def get_log(self, max_entries=1 << 20):
+        arr = (LogEntry * max_entries)()
+        n = self._check(self.lib.fredopt_get_log(self.h, arr, max_entries))
+        return [{k: getattr(arr[i], k) for k, _ in LogEntry._fields_} for i in range(n)]
+
+    def get_state(self):
+        w = np.empty(self.n_spots, np.float32)
+        k, s = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.fredopt_get_state(self.h, w.ctypes.data, ctypes.byref(k), ctypes.byref(s), 0))
+        return w, k.value, s.value
+
+    def set_state(self, w, k, s):
+        dev = _on_device(w)
+        p, keep = _ptr(w, np.float32)
+        self._check(self.lib.fredopt_set_state(self.h, p, int(k), int(s), DEVICE_PTR if dev else 0))
+
+    # ---------------------------------------------------------- single passes
+    def forward(self, w):
+        dev = _on_device(w)
+        d, l = self._out(dev, self.n_vox), self._out(dev, self.n_vox)
+        self._check(self.lib.fredopt_forward(self.h, _ptr(w, np.float32)[0], _ptr(d, np.float32)[0],
+                                             _ptr(l, np.float32)[0], DEVICE_PTR if dev else 0))
+        return d, l
+
+    def backward(self, a_D, a_L):
+        dev = _on_device(a_D if a_D is not None else a_L)
+        u = self._out(dev, self.n_spots)
+        self._check(self.lib.fredopt_backward(self.h, _ptr(a_D, np.float32)[0], _ptr(a_L, np.float32)[0],
+                                              _ptr(u, np.float32)[0], DEVICE_PTR if dev else 0))
+        return u
+
+    def feasibility_step(self, x, relaxation=1.0, prio_scale=1.0, norm="all"):
+        dev = _on_device(x)
+        w = self._out(dev, self.n_spots)
+        self._check(self.lib.fredopt_feasibility_step(self.h, _ptr(x, np.float32)[0], float(relaxation),
+                                                      float(prio_scale), NORMS[norm], _ptr(w, np.float32)[0],
+                                                      DEVICE_PTR if dev else 0))
+        return w
+
+    def objective(self, x):
+        dev = _on_device(x)
+        g = self._out(dev, self.n_spots)
+        f = ctypes.c_double()
+        self._check(self.lib.fredopt_objective(self.h, _ptr(x, np.float32)[0], ctypes.byref(f),
+                                               _ptr(g, np.float32)[0], DEVICE_PTR if dev else 0))
+        return f.value, g
+
+    # ---------------------------------------------------------- inspection
+    def get_rows(self):
+        sz = self.sizes()
+        vox = np.empty(sz["n_rows"], np.int64)
+        mask = np.empty(sz["n_rows"], np.uint32)
+        self._check(self.lib.fredopt_get_rows(self.h, vox.ctypes.data, mask.ctypes.data))
+        return vox, mask
+
+    def get_csc(self):
+        sz = self.sizes()
+        cp = np.empty(sz["n_spots"] + 1, np.int64)
+        row = np.empty(max(1, sz["nnz_rows"]), np.int32)
+        D = np.empty(max(1, sz["nnz_rows"]), np.float32)
+        L = np.empty(max(1, sz["nnz_rows"]), np.float32)
+        self._check(self.lib.fredopt_get_csc(self.h, cp.ctypes.data, row.ctypes.data, D.ctypes.data, L.ctypes.data))
+        m = sz["nnz_rows"]
+        return cp, row[:m], D[:m], L[:m]
+
+    def get_moments(self):
+        n = self.sizes()["n_rows"]
+        a, b, c = (np.empty(max(1, n), np.float64) for _ in range(3))
+        self._check(self.lib.fredopt_get_moments(self.h, a.ctypes.data, b.ctypes.data, c.ctypes.data))
+        return a[:n], b[:n], c[:n]
+
+    def set_timing(self, enable: bool):
+        self._check(self.lib.fredopt_set_timing(self.h, 1 if enable else 0))
+
+    def get_timing(self):
+        ms = (ctypes.c_double * KCLASS_N)()
+        cnt = (ctypes.c_int64 * KCLASS_N)()
+        self._check(self.lib.fredopt_get_timing(self.h, ms, cnt))
+        return {KCLASS_NAMES[i]: (ms[i], cnt[i]) for i in range(KCLASS_N)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.fredopt_launch_count(self.h))

@@ -304,11 +304,12 @@ def clinical_structures(shape=CLIN_SHAPE, h=CLIN_H):
     return mask
 
 
-def clinical_plan(seed: int = 0, noise: float = 0.01, iters: int = 500, **kw) -> Plan:
+def clinical_plan(seed: int = 0, noise: float = 0.01, iters: int = 500, shape=CLIN_SHAPE, h=CLIN_H,
+                  **kw) -> Plan:
     """Plain method, clinical size: 200x200x150 voxels at 2 mm, 3 fields, 30000
     spots; PTV 150 cc at 2 Gy within [0.95, 1.07]; brainstem-like Dmax 1.2 Gy,
     chiasm-like Dmax 1.0 Gy, eye-like Dmax 0.5 Gy; LETd <= 2.5 / 2.5 / 3.0 keV/um."""
-    p = clinical_params(seed=seed, noise=noise, **kw)
+    p = clinical_params(seed=seed, noise=noise, shape=shape, h=h, **kw)
     row_ptr, col, D, L = generate(p)
     structures = [dict(name="PTV", bit=0, role="target"), dict(name="brainstem", bit=1, role="oar"),
                   dict(name="chiasm", bit=2, role="oar"), dict(name="eyes", bit=3, role="oar")]
@@ -323,8 +324,8 @@ def clinical_plan(seed: int = 0, noise: float = 0.01, iters: int = 500, **kw) ->
         dict(struct_bit=3, kind="LETD_MAX", bound=3.0, priority=1.0),
     ]
     n = int(p.n_fields * p.n_layers * p.spots_x * p.spots_y)
-    return Plan(name="clinical", shape=tuple(CLIN_SHAPE), h_mm=CLIN_H, params=p, row_ptr=row_ptr,
-                col=col, D=D, L=L, mask=clinical_structures(), structures=structures,
+    return Plan(name="clinical", shape=tuple(shape), h_mm=h, params=p, row_ptr=row_ptr,
+                col=col, D=D, L=L, mask=clinical_structures(shape, h), structures=structures,
                 constraints=constraints, objective=default_objective(structures, constraints),
                 w0=np.ones(n, np.float32), iters=iters, alpha=0.99, relaxation=1.0)
 

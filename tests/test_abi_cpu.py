@@ -1,0 +1,67 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function that include/fredopt.h declares; argument errors that need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2509_20012_gb300 import fredopt
+    return fredopt.load_library()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "fredopt.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fredopt_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fredopt_load_influence", "fredopt_set_constraints", "fredopt_superiorize",
+                     "fredopt_create", "fredopt_destroy", "fredopt_get_state", "fredopt_set_state",
+                     "fredopt_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2509_20012_gb300 import fredopt
+    assert set(declared_functions()) <= set(fredopt._SIGS)
+
+
+def test_strerror_and_defaults(lib):
+    from paper_2509_20012_gb300 import fredopt
+    assert lib.fredopt_strerror(0) == b"ok"
+    assert lib.fredopt_strerror(-3) == b"pattern"
+    assert lib.fredopt_strerror(-99) == b"unknown error"
+    p = fredopt.default_params()
+    assert p.beta0 < 0 and p.eta == 1.0 and p.reductions == 1 and p.max_trials == 50
+    assert p.c_cdl == pytest.approx(0.04) and p.use_graphs == 1
+
+
+def test_null_and_bad_arguments_without_gpu(lib):
+    assert lib.fredopt_create(None, 0, None) == -1
+    assert lib.fredopt_destroy(None) == -1
+    assert lib.fredopt_launch_count(None) == -1
+    h = ctypes.c_void_p()
+    # no device with this index (and on a CPU-only machine none at all)
+    assert lib.fredopt_create(ctypes.byref(h), 1 << 20, None) == -1
+    assert lib.fredopt_iterate(None, 1) == -1
+
+
+def test_kernels_compiled_for_sm_103a():
+    src = open(os.path.join(ROOT, "paper_2509_20012_gb300", "_build.py")).read()
+    assert "arch=compute_103a,code=sm_103a" in src

@@ -1,0 +1,418 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: bit-exact for masks, row order, sparsity pattern and the CSC
+copy; <= 1e-5 relative for one FP32 product (relative to the sum of absolute
+products of the row or column, which equals |result| for nonnegative
+operands); <= 1e-4 relative L2 for w after 100 iterations; final constraint
+violations and dose within 1e-4 x prescription (2 Gy) of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import phantom
+
+pytestmark = pytest.mark.gpu
+
+PRESC = 2.0
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2509_20012_gb300 import fredopt
+    return fredopt
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    pl = phantom.tiny_plan()
+    P = oracle.build_problem(pl.row_ptr, pl.col, pl.D, pl.L, pl.n_spots, pl.mask, pl.constraints,
+                             pl.objective)
+    return pl, P, oracle.constraint_rows(P)
+
+
+def handle(lib, plan, fmt="fp32", rows="all"):
+    h = lib.Handle(0)
+    h.load_plan(plan, fmt=fmt, rows=rows)
+    return h
+
+
+def abs_sum_bound(Mabs, xabs):
+    return Mabs @ xabs
+
+
+def hot_rows(plan, rows):
+    if rows == "all":
+        return np.arange(plan.n_vox)
+    return np.nonzero(plan.mask)[0]
+
+
+# ---------------------------------------------------------------- setup (K5)
+
+@pytest.mark.parametrize("rows", ["all", "roi"])
+def test_rows_masks_bit_exact(lib, tiny, rows):
+    pl, P, R = tiny
+    with handle(lib, pl, rows=rows) as h:
+        vox, mask = h.get_rows()
+    np.testing.assert_array_equal(vox, hot_rows(pl, rows))
+    np.testing.assert_array_equal(mask, pl.mask[vox])
+
+
+@pytest.mark.parametrize("rows", ["all", "roi"])
+def test_csc_bit_exact(lib, tiny, rows):
+    pl, P, R = tiny
+    hr = hot_rows(pl, rows)
+    sub_D = P.D[hr]
+    sub_L = P.L[hr]
+    rp = sub_D.indptr.astype(np.int64)
+    col = sub_D.indices.astype(np.int32)
+    Dv = sub_D.data.astype(np.float32)
+    Lv = sub_L.data.astype(np.float32)
+    cp, row, DT, LT = oracle.transpose_csr(rp, col, pl.n_spots, Dv, Lv)
+    with handle(lib, pl, rows=rows) as h:
+        gcp, grow, gD, gL = h.get_csc()
+    np.testing.assert_array_equal(gcp, cp)
+    np.testing.assert_array_equal(grow, row)
+    np.testing.assert_array_equal(gD.view(np.uint32), DT.view(np.uint32))
+    np.testing.assert_array_equal(gL.view(np.uint32), LT.view(np.uint32))
+
+
+def test_moments_fp64(lib, tiny):
+    pl, P, R = tiny
+    with handle(lib, pl, rows="roi") as h:
+        dd, ll, dl = h.get_moments()
+    hr = hot_rows(pl, "roi")
+    D, L = P.D[hr], P.L[hr]
+    np.testing.assert_allclose(dd, np.asarray(D.multiply(D).sum(1)).ravel(), rtol=1e-12)
+    np.testing.assert_allclose(ll, np.asarray(L.multiply(L).sum(1)).ravel(), rtol=1e-12)
+    np.testing.assert_allclose(dl, np.asarray(D.multiply(L).sum(1)).ravel(), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- single passes
+
+@pytest.mark.parametrize("rows", ["all", "roi"])
+def test_forward_fp32(lib, tiny, rows):
+    pl, P, R = tiny
+    rng = np.random.default_rng(1)
+    w = rng.uniform(0.0, 2.0, pl.n_spots).astype(np.float32)
+    with handle(lib, pl, rows=rows) as h:
+        dose, lw = h.forward(w)
+    d_ref, l_ref = oracle.forward(P, w)
+    np.testing.assert_array_less(np.abs(dose - d_ref), 1e-5 * np.abs(d_ref) + 1e-30)
+    np.testing.assert_array_less(np.abs(lw - l_ref), 1e-5 * np.abs(l_ref) + 1e-30)
+    # signed input: bound by the sum of absolute products
+    w2 = rng.normal(size=pl.n_spots).astype(np.float32)
+    with handle(lib, pl, rows=rows) as h:
+        dose, lw = h.forward(w2)
+    d_ref, l_ref = oracle.forward(P, w2)
+    bd = abs(P.D) @ np.abs(w2.astype(np.float64))
+    bl = abs(P.L) @ np.abs(w2.astype(np.float64))
+    assert np.all(np.abs(dose - d_ref) <= 1e-5 * bd + 1e-30)
+    assert np.all(np.abs(lw - l_ref) <= 1e-5 * bl + 1e-30)
+
+
+@pytest.mark.parametrize("rows", ["all", "roi"])
+def test_backward_fp32(lib, tiny, rows):
+    pl, P, R = tiny
+    rng = np.random.default_rng(2)
+    aD = rng.normal(size=pl.n_vox).astype(np.float32)
+    aL = rng.normal(size=pl.n_vox).astype(np.float32)
+    hr = hot_rows(pl, rows)
+    mD = np.zeros(pl.n_vox)
+    mL = np.zeros(pl.n_vox)
+    mD[hr] = aD[hr]
+    mL[hr] = aL[hr]
+    ref = P.D.T @ mD + P.L.T @ mL
+    bound = abs(P.D).T @ np.abs(mD) + abs(P.L).T @ np.abs(mL)
+    with handle(lib, pl, rows=rows) as h:
+        u = h.backward(aD, aL)
+    assert np.all(np.abs(u - ref) <= 1e-5 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("norm", ["all", "violated"])
+def test_feasibility_step(lib, tiny, norm):
+    pl, P, R = tiny
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0.0, 2.0, pl.n_spots).astype(np.float32)
+    for lam, ps in ((1.0, 1.0), (1.7, 0.6)):
+        ref = oracle.cimmino_step(R, x, lam, prio_scale=ps, norm=norm)
+        with handle(lib, pl) as h:
+            got = h.feasibility_step(x, lam, ps, norm)
+        step = np.linalg.norm(ref - x)
+        assert np.linalg.norm(got - ref) <= 1e-5 * max(step, 1e-12) + 1e-6 * np.linalg.norm(ref)
+
+
+def test_objective_and_gradient(lib, tiny):
+    pl, P, R = tiny
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0.0, 2.0, pl.n_spots).astype(np.float32)
+    P2 = oracle.Problem(P.D, P.L, P.mask, P.constraints,
+                        [dict(struct_bit=0, quantity="DOSE", target=2.0, weight=0.5)] + list(pl.objective))
+    for prob, terms in ((P, pl.objective), (P2, P2.objective)):
+        with lib.Handle(0) as h:
+            h.load_plan(pl)
+            h.set_objective(terms)
+            f, g = h.objective(x)
+        f_ref = oracle.objective(prob, x)
+        g_ref = oracle.objective_gradient(prob, x)
+        assert f == pytest.approx(f_ref, rel=1e-5)
+        assert np.linalg.norm(g - g_ref) <= 1e-5 * np.linalg.norm(g_ref)
+
+
+# ---------------------------------------------------------------- whole loop
+
+def run_gpu(lib, pl, iters, rows="all", fmt="fp32", **params):
+    with handle(lib, pl, fmt=fmt, rows=rows) as h:
+        w, dose, letd, rep = h.superiorize(pl.w0, iters, pl.alpha, pl.relaxation, **params)
+        log = h.get_log()
+    return w, dose, letd, rep, log
+
+
+def violation_by_kind(pl, P, w):
+    dose, lw = oracle.forward(P, w)
+    let = oracle.letd(dose, lw)
+    out = {}
+    for ci, c in enumerate(pl.constraints):
+        sel = ((pl.mask >> np.uint32(c["struct_bit"])) & 1).astype(bool)
+        if c["kind"] == "DOSE_MIN":
+            v = c["bound"] - dose[sel]
+        elif c["kind"] == "DOSE_MAX":
+            v = dose[sel] - c["bound"]
+        elif c["kind"] == "LETD_MAX":
+            sel = sel & (dose > 0)
+            v = let[sel] - c["bound"]
+        else:
+            continue
+        out[ci] = float(max(v.max(), 0.0)) if v.size else 0.0
+    return out
+
+
+@pytest.mark.parametrize("rows", ["all", "roi"])
+def test_superiorize_100_iterations(lib, tiny, rows):
+    pl, P, R = tiny
+    w_ref, log_ref = oracle.superiorize(P, pl.w0, 100, pl.alpha, pl.relaxation, rows=R)
+    w, dose, letd, rep, log = run_gpu(lib, pl, 100, rows=rows)
+    rel = np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref)
+    assert rel <= 1e-4, rel
+    # identical accept/reject decisions and trial counters
+    assert [e["s"] for e in log] == [e["s"] for e in log_ref]
+    assert [e["accepted"] for e in log] == [e["accepted"] for e in log_ref]
+    for e, r in zip(log, log_ref):
+        assert e["f_end"] <= e["f_start"]
+        assert e["f_start"] == pytest.approx(r["f_start"], rel=1e-4, abs=1e-12)
+    d_ref, l_ref = oracle.forward(P, w_ref)
+    assert np.max(np.abs(dose - d_ref)) <= 1e-4 * PRESC
+    vg = violation_by_kind(pl, P, w.astype(np.float64))
+    vr = violation_by_kind(pl, P, w_ref)
+    for ci in vr:
+        # dose: 1e-4 of prescription; LETd (keV/um, up to 15): the 1e-4 relative
+        # tolerance of w carried to a 15 keV/um LETd, rounded up
+        tol = 1e-4 * PRESC if pl.constraints[ci]["kind"].startswith("DOSE") else 2e-3
+        assert abs(vg[ci] - vr[ci]) <= tol, (ci, vg[ci], vr[ci])
+    assert rep["iters"] == 100
+    assert rep["objective"] == pytest.approx(oracle.objective(P, w.astype(np.float64)), rel=1e-9)
+    assert rep["unreachable_rows"] == R.unreachable
+    assert rep["n_rows"] == R.A.shape[0]
+
+
+def test_plain_cimmino_matches(lib, tiny):
+    pl, P, R = tiny
+    w_ref, _ = oracle.superiorize(P, pl.w0, 30, pl.alpha, pl.relaxation, rows=R, reductions=0)
+    w, *_ = run_gpu(lib, pl, 30, reductions=0)
+    assert np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("opts", [dict(reductions=2), dict(eta=0.95), dict(cimmino_norm="violated"),
+                                  dict(grad_normalize=0, beta0=50.0), dict(beta0=1.0, max_trials=3)],
+                         ids=["N2", "eta", "violated", "raw_grad", "cap"])
+def test_variants_match(lib, tiny, opts):
+    pl, P, R = tiny
+    o = dict(opts)
+    norm = o.pop("cimmino_norm", "all")
+    kw = dict(eta=o.get("eta", 1.0), reductions=o.get("reductions", 1), norm=norm,
+              grad_normalize=bool(o.get("grad_normalize", 1)), max_trials=o.get("max_trials", 50))
+    if "beta0" in o:
+        kw["beta0"] = o["beta0"]
+    w_ref, log_ref = oracle.superiorize(P, pl.w0, 15, pl.alpha, pl.relaxation, rows=R, **kw)
+    w, d, l, rep, log = run_gpu(lib, pl, 15, cimmino_norm=norm, **o)
+    assert [e["s"] for e in log] == [e["s"] for e in log_ref]
+    assert np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref) <= 1e-4
+
+
+def test_deterministic_and_graph_equals_plain(lib, tiny):
+    pl, P, R = tiny
+    w1, *_ = run_gpu(lib, pl, 20)
+    w2, *_ = run_gpu(lib, pl, 20)
+    w3, *_ = run_gpu(lib, pl, 20, use_graphs=0)
+    np.testing.assert_array_equal(w1, w2)
+    np.testing.assert_array_equal(w1, w3)
+
+
+def test_checkpoint_resume_bit_exact(lib, tiny):
+    pl, P, R = tiny
+    with handle(lib, pl) as h:
+        h.begin(pl.w0, pl.alpha, pl.relaxation)
+        h.iterate(20)
+        w_full, *_ = h.end()
+    with handle(lib, pl) as h:
+        h.begin(pl.w0, pl.alpha, pl.relaxation)
+        h.iterate(10)
+        w_mid, k, s = h.get_state()
+    assert k == 10
+    beta0 = 0.1 * float(np.linalg.norm(pl.w0.astype(np.float64)))
+    with handle(lib, pl) as h:
+        h.begin(w_mid, pl.alpha, pl.relaxation, beta0=beta0)
+        h.set_state(w_mid, k, s)
+        h.iterate(10)
+        w_res, *_ = h.end()
+    np.testing.assert_array_equal(w_res, w_full)
+
+
+def test_device_pointers(lib, tiny):
+    torch = pytest.importorskip("torch")
+    pl, P, R = tiny
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    with lib.Handle(0) as h:
+        h.load_influence(t(pl.row_ptr), t(pl.col), t(pl.D), t(pl.L), t(pl.mask.view(np.int32)), pl.n_spots)
+        h.set_constraints(pl.constraints)
+        h.set_objective(pl.objective)
+        w, dose, letd, rep = h.superiorize(t(pl.w0), 10, pl.alpha, pl.relaxation)
+        assert w.is_cuda
+    w_host, *_ = run_gpu(lib, pl, 10)
+    np.testing.assert_array_equal(w.cpu().numpy(), w_host)
+
+
+# ---------------------------------------------------------------- precision
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_quantized_storage(lib, tiny, fmt):
+    """16-bit storage with power-of-two row scales: the product equals the
+    FP64 product of the dequantised matrix within FP32 accumulation error,
+    the CSC copy is the exact transpose of the stored values, and the dose
+    error against the FP32 oracle is reported (bounded by the format)."""
+    pl, P, R = tiny
+    with handle(lib, pl, fmt=fmt) as h:
+        cp, row, DT, LT = h.get_csc()
+        dose, lw = h.forward(pl.w0)
+    # the dequantised matrix, rebuilt from the exact CSC values
+    import scipy.sparse as sp
+    Dq = sp.csc_matrix((DT.astype(np.float64), row, cp), shape=(pl.n_vox, pl.n_spots))
+    Lq = sp.csc_matrix((LT.astype(np.float64), row, cp), shape=(pl.n_vox, pl.n_spots))
+    d_ref = Dq @ pl.w0.astype(np.float64)
+    np.testing.assert_array_less(np.abs(dose - d_ref), 1e-5 * np.abs(d_ref) + 1e-30)
+    rel_elem = np.abs(DT - P.D.tocsc().data.astype(np.float32)) / np.abs(P.D.tocsc().data)
+    assert rel_elem.max() <= (2.0 ** -8 if fmt == "bf16" else 2.0 ** -11) * 1.0001
+    d32, _ = oracle.forward(P, pl.w0)
+    err = np.max(np.abs(dose - d32)) / PRESC
+    assert err <= (4e-3 if fmt == "bf16" else 5e-4)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def small_plan(row_ptr, col, D, L, n_spots, mask, cons, obj, iters=5):
+    return phantom.Plan(name="small", shape=(len(row_ptr) - 1, 1, 1), h_mm=1.0, params=None,
+                        row_ptr=row_ptr, col=col, D=D, L=L, mask=mask, structures=[], constraints=cons,
+                        objective=obj, w0=np.ones(n_spots, np.float32), iters=iters, alpha=0.9,
+                        relaxation=1.0)
+
+
+@pytest.mark.parametrize("n_rows,n_cols,density,empty", [(37, 5, 0.5, 4), (300, 129, 0.2, 30),
+                                                         (1000, 1, 0.7, 100), (64, 3000, 0.3, 0)])
+def test_ragged_random_plans(lib, n_rows, n_cols, density, empty):
+    rp, col, D, L = phantom.random_csr(n_rows, n_cols, density, seed=n_rows + n_cols, empty_rows=empty)
+    rng = np.random.default_rng(5)
+    mask = rng.integers(0, 4, n_rows).astype(np.uint32)
+    cons = [dict(struct_bit=0, kind="DOSE_MIN", bound=2.0, priority=1.0),
+            dict(struct_bit=0, kind="DOSE_MAX", bound=3.0, priority=2.0),
+            dict(struct_bit=1, kind="CDL_MAX", bound=0.5, priority=1.0),
+            dict(struct_bit=1, kind="LETD_MAX", bound=4.0, priority=0.5)]
+    obj = [dict(struct_bit=1, quantity="CDL", target=0.0, weight=1.0),
+           dict(struct_bit=0, quantity="DOSE", target=2.5, weight=0.3)]
+    pl = small_plan(rp, col, D, L, n_cols, mask, cons, obj)
+    P = oracle.build_problem(rp, col, D, L, n_cols, mask, cons, obj)
+    w_ref, log_ref = oracle.superiorize(P, pl.w0, 8, 0.9, 1.0)
+    for rows in ("all", "roi"):
+        w, dose, letd, rep, log = run_gpu(lib, pl, 8, rows=rows)
+        assert [e["s"] for e in log] == [e["s"] for e in log_ref]
+        assert np.linalg.norm(w - w_ref) <= 1e-4 * max(np.linalg.norm(w_ref), 1e-12)
+        d_ref, l_ref = oracle.forward(P, w_ref)
+        np.testing.assert_allclose(dose, d_ref, rtol=1e-4, atol=1e-6)
+        lt = oracle.letd(d_ref, l_ref)
+        np.testing.assert_allclose(letd, lt, rtol=1e-4, atol=1e-6)
+
+
+def test_empty_matrix_and_no_constraints(lib):
+    rp = np.zeros(11, np.int64)
+    pl = small_plan(rp, np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros(0, np.float32), 6,
+                    np.ones(10, np.uint32), [], [])
+    w, dose, letd, rep, log = run_gpu(lib, pl, 3)
+    np.testing.assert_array_equal(w, np.ones(6, np.float32))
+    np.testing.assert_array_equal(dose, 0)
+    np.testing.assert_array_equal(letd, 0)
+
+
+def test_input_errors_leave_handle_usable(lib, tiny):
+    pl, P, R = tiny
+    bad_col = pl.col.copy()
+    bad_col[5] = pl.n_spots + 3
+    with lib.Handle(0) as h:
+        with pytest.raises(lib.FredoptError) as e:
+            h.load_influence(pl.row_ptr, bad_col, pl.D, pl.L, pl.mask, pl.n_spots)
+        assert e.value.code == -3
+        unsorted = pl.col.copy()
+        r = int(np.nonzero(np.diff(pl.row_ptr) >= 2)[0][0])
+        p0 = pl.row_ptr[r]
+        unsorted[p0], unsorted[p0 + 1] = unsorted[p0 + 1], unsorted[p0]
+        with pytest.raises(lib.FredoptError) as e:
+            h.load_influence(pl.row_ptr, unsorted, pl.D, pl.L, pl.mask, pl.n_spots)
+        assert e.value.code == -3
+        nanD = pl.D.copy()
+        nanD[7] = np.nan
+        with pytest.raises(lib.FredoptError) as e:
+            h.load_influence(pl.row_ptr, pl.col, nanD, pl.L, pl.mask, pl.n_spots)
+        assert e.value.code == -4
+        bad_rp = pl.row_ptr.copy()
+        bad_rp[10] = bad_rp[11] + 1
+        with pytest.raises(lib.FredoptError) as e:
+            h.load_influence(bad_rp, pl.col, pl.D, pl.L, pl.mask, pl.n_spots)
+        assert e.value.code == -3
+        with pytest.raises(lib.FredoptError) as e:
+            h.iterate(1)
+        assert e.value.code == -5
+        h.load_plan(pl)
+        for bad in (dict(alpha=1.0), dict(alpha=0.0), dict(relaxation=2.5), dict(relaxation=0.0)):
+            a = bad.get("alpha", 0.99)
+            lam = bad.get("relaxation", 1.0)
+            with pytest.raises(lib.FredoptError) as e:
+                h.begin(pl.w0, a, lam)
+            assert e.value.code == -1
+        neg = pl.w0.copy()
+        neg[0] = -1
+        with pytest.raises(lib.FredoptError):
+            h.begin(neg, 0.99, 1.0)
+        with pytest.raises(lib.FredoptError):
+            h.set_constraints([dict(struct_bit=40, kind="DOSE_MAX", bound=1.0, priority=1.0)])
+        # still usable
+        w, dose, letd, rep = h.superiorize(pl.w0, 5, 0.99, 1.0)
+    w_ok, *_ = run_gpu(lib, pl, 5)
+    np.testing.assert_array_equal(w, w_ok)
+
+
+def test_launch_count_and_timing(lib, tiny):
+    pl, P, R = tiny
+    with handle(lib, pl) as h:
+        h.set_timing(True)
+        h.begin(pl.w0, pl.alpha, pl.relaxation)
+        h.iterate(4)
+        h.end()
+        t = h.get_timing()
+        n = h.launch_count()
+    # per iteration: 2 forward, 2 transposed, 2 column finishes, 1 scalar finish, 1 constraint kernel
+    assert t["forward"][1] == 2 * 4 + 1
+    assert t["backward"][1] == 2 * 4
+    assert t["constraints"][1] == 4
+    assert n >= 8 * 4
+    assert all(ms >= 0 for ms, c in t.values())
