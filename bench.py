@@ -102,18 +102,19 @@ class ClockSampler:
 
 def fwd_bytes(nnz, rows, vb, n_launch_obj, n_launch_bc):
     """Algorithmic bytes of the forward launches: the shared index stream
-    (4 B) and both value streams (vb B each) per nonzero, row_ptr (8 B) and
-    the (Dx, Lx) pair (8 B) per row; OBJ adds mask (4) + residual (8) per row,
-    BC adds mask (4) + residual read (8) per row."""
-    base = nnz * (4 + 2 * vb) + rows * (8 + 8)
-    return (n_launch_obj + n_launch_bc) * (base + rows * 12)
+    (4 B) and both value streams (vb B each) per nonzero; per row with
+    nonzeros: row_ptr (8 B), the (Dx, Lx) pair (8 B), mask (4 B) and the
+    residual pair written (OBJ) or read (BC) (8 B).  16-bit storage adds the
+    two row scales (8 B)."""
+    base = nnz * (4 + 2 * vb) + rows * (8 + 8 + 12 + (8 if vb == 2 else 0))
+    return (n_launch_obj + n_launch_bc) * base
 
 
 def bwd_bytes(nnz, n_hot, n_chunks, vb, n_grad, n_proj):
     """Transposed launches: row index (4 B) + L (vb) [+ D (vb) for the
     projection pass, and for a gradient with DOSE terms] per nonzero, the
-    coefficient pair read once (8 B per row), chunk pointer (8 B) and chunk
-    sum (4 B) per chunk."""
+    coefficient pair read once per row with nonzeros (8 B), chunk pointer
+    (8 B) and chunk sum (4 B) per chunk."""
     g = nnz * (4 + vb) + n_hot * 8 + n_chunks * 12
     p = nnz * (4 + 2 * vb) + n_hot * 8 + n_chunks * 12
     return n_grad * g + n_proj * p
@@ -183,10 +184,12 @@ def run_gpu_arm(args):
         nf = kt["forward"][1]
         nb = kt["backward"][1]
         n_iter = args.steps
-        fb = fwd_bytes(sz["nnz_rows"], sz["n_rows"], vb, n_iter, n_iter)
+        hot = np.ones(plan.n_vox, bool) if rows == "all" else plan.mask != 0
+        rows_nz = int(np.count_nonzero(hot & (np.diff(plan.row_ptr) > 0)))
+        fb = fwd_bytes(sz["nnz_rows"], rows_nz, vb, n_iter, n_iter)
         # chunk count is internal; it is small next to nnz (bounded by nnz/256 + n_spots)
         n_chunks_est = sz["nnz_rows"] // 2048 + sz["n_spots"]
-        bb = bwd_bytes(sz["nnz_rows"], sz["n_rows"], n_chunks_est, vb, n_iter, n_iter)
+        bb = bwd_bytes(sz["nnz_rows"], rows_nz, n_chunks_est, vb, n_iter, n_iter)
         f_ms, b_ms = kt["forward"][0], kt["backward"][0]
         fw = {"bound": "hbm", "achieved": fb / (f_ms * 1e-3) / 1e9 if f_ms else None, "peak": hbm,
               "unit": "GB/s", "kernel": "k_forward (fused Dx/Lx)", "launches": nf, "ms_total": f_ms,

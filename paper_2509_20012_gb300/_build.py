@@ -43,16 +43,19 @@ def needs_build() -> bool:
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, lib: str = LIB, defines=()) -> str:
+    """Compile the library to `lib`; `defines` are extra -D macros."""
     with _lock:
-        if not force and not needs_build():
+        if not force and lib == LIB and not needs_build():
             return LIB
-        os.makedirs(BUILD, exist_ok=True)
+        bdir = BUILD if lib == LIB else lib + ".objs"
+        os.makedirs(bdir, exist_ok=True)
         objs, procs = [], []
         for src in SOURCES:
-            obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+            obj = os.path.join(bdir, src.replace(".cu", ".o"))
             objs.append(obj)
-            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *[f"-D{d}" for d in defines], "-c",
+                   os.path.join(CSRC, src), "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -60,13 +63,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             out, _ = p.communicate()
             if p.returncode != 0:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{out.decode(errors='replace')}")
-        tmp = LIB + f".{os.getpid()}.tmp"
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout.decode(errors='replace')}")
-        os.replace(tmp, LIB)
-        return LIB
+        os.replace(tmp, lib)
+        return lib
 
 
 if __name__ == "__main__":

@@ -67,12 +67,14 @@ struct fredopt_ctx {
   int fmt = 0;
   bool roi = false;
   int64_t V = 0, nnz = 0, n_hot = 0, nnz_hot = 0;
+  int64_t n_hot_ne = 0, n_cold_ne = 0;  // rows with nonzeros among streamed / other rows
+  bool perm = false;                    // device order differs from voxel order
   int32_t n = 0, n_pad = 0;
   DBuf<int64_t> rp;
   DBuf<int32_t> col;
   DBuf<uint8_t> Dv, Lv;
   DBuf<float> sD, sL;
-  DBuf<int64_t> voxel;  // only with ROI
+  DBuf<int64_t> voxel;  // device row -> voxel (when perm)
   DBuf<uint32_t> mask;  // [n_hot]
   DBuf<double> mdd, mll, mdl;
   DBuf<int64_t> cp;
@@ -82,7 +84,7 @@ struct fredopt_ctx {
   DBuf<int32_t> col_chunk, warp_chunk;
   int64_t n_chunks = 0;
   bool hint_fwd = true, hint_bwd = true;
-  std::vector<int64_t> h_voxel;  // device row -> voxel (host copy)
+  std::vector<int64_t> h_voxel;  // device row -> voxel (host copy, when perm)
   std::vector<uint32_t> h_mask;  // per streamed row
 
   // problem
@@ -204,6 +206,60 @@ std::vector<int64_t> partition_rows(const std::vector<int64_t>& rp, int64_t n_ro
   return b;
 }
 
+// Row ranges [r0, r1) for `parts` warps over the union of the row ranges
+// `ranges` (each split in nnz-balanced contiguous pieces; warps are shared
+// among ranges in proportion to their cost).  Returns 2*parts values.
+std::vector<int64_t> partition_pairs(const std::vector<int64_t>& rp,
+                                     const std::vector<std::pair<int64_t, int64_t>>& ranges, int parts,
+                                     int64_t row_cost) {
+  std::vector<int64_t> out(2 * (size_t)parts, 0);
+  std::vector<size_t> live;
+  double total = 0.0;
+  std::vector<double> cost(ranges.size(), 0.0);
+  for (size_t k = 0; k < ranges.size(); ++k) {
+    const int64_t a = ranges[k].first, z = ranges[k].second;
+    if (z <= a) continue;
+    cost[k] = (double)(rp[z] - rp[a]) + (double)row_cost * (double)(z - a);
+    total += cost[k];
+    live.push_back(k);
+  }
+  int used = 0;
+  for (size_t i = 0; i < live.size(); ++i) {
+    const size_t k = live[i];
+    const int later = (int)(live.size() - 1 - i);
+    int w;
+    if (later == 0) {
+      w = parts - used;
+    } else {
+      w = (int)std::llround(parts * (total > 0 ? cost[k] / total : 0.0));
+      w = std::max(1, std::min(w, parts - used - later));
+    }
+    if (w <= 0) break;
+    const int64_t a = ranges[k].first, z = ranges[k].second;
+    const double tot = cost[k];
+    int64_t lo = a;
+    for (int j = 0; j < w; ++j) {
+      int64_t x = z;
+      if (j + 1 < w) {
+        const double target = tot * (j + 1) / w;
+        int64_t y = z;
+        x = lo;
+        while (x < y) {  // first row m with prefix(m) >= target
+          const int64_t m = (x + y) / 2;
+          const double pre = (double)(rp[m] - rp[a]) + (double)row_cost * (double)(m - a);
+          if (pre < target) x = m + 1;
+          else y = m;
+        }
+      }
+      out[2 * (used + j)] = lo;
+      out[2 * (used + j) + 1] = x;
+      lo = x;
+    }
+    used += w;
+  }
+  return out;
+}
+
 template <typename T>
 cudaError_t upload_vec(fredopt_t h, DBuf<T>& d, const std::vector<T>& v) {
   cudaError_t e = d.alloc(v.size());
@@ -271,7 +327,7 @@ FwdArgs fwd_args(fredopt_t h, bool hot) {
   a.n_hot = h->n_hot;
   a.n_warps = h->geo.fwd_warps;
   a.st = h->st.p;
-  a.voxel = h->roi ? h->voxel.p : nullptr;
+  a.voxel = h->perm ? h->voxel.p : nullptr;
   return a;
 }
 
@@ -379,6 +435,19 @@ void enqueue_iteration(fredopt_t h) {
   cc.lam = h->lam;
   cc.in_solve = 1;
   run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
+}
+
+// Objective (Eq. 2 terms) of the streamed rows without nonzeros: their dose
+// and LET-weighted dose are 0 for every w, so each term contributes w*T^2.
+double f_empty(fredopt_t h) {
+  double f = 0.0;
+  for (int64_t r = h->n_hot_ne; r < h->n_hot; ++r) {
+    const uint32_t m = h->h_mask[r];
+    if (!m) continue;
+    for (int i = 0; i < h->tab.n_obj; ++i)
+      if ((m >> h->tab.obj[i].bit) & 1u) f += h->tab.obj[i].weight * h->tab.obj[i].target * h->tab.obj[i].target;
+  }
+  return f;
 }
 
 int need_loaded(fredopt_t h) {
@@ -529,24 +598,30 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   for (int64_t i = 0; i < n_vox; ++i)
     if (rp0[i + 1] < rp0[i]) return fail(h, FREDOPT_ERR_PATTERN, "row_ptr not monotone");
 
-  // ---- device order of rows
-  std::vector<int64_t> order;  // device row -> voxel
-  int64_t n_hot = n_vox;
-  if (roi) {
-    order.reserve(n_vox);
-    for (int64_t i = 0; i < n_vox; ++i)
-      if (m0[i]) order.push_back(i);
-    n_hot = (int64_t)order.size();
-    for (int64_t i = 0; i < n_vox; ++i)
-      if (!m0[i]) order.push_back(i);
-  }
+  // ---- device order of rows: streamed rows with nonzeros, streamed rows
+  // without, other rows with nonzeros, other rows without (each ascending)
+  std::vector<int64_t> order;
+  order.reserve(n_vox);
+  auto is_hot = [&](int64_t i) { return !roi || m0[i] != 0; };
+  auto has_nz = [&](int64_t i) { return rp0[i + 1] > rp0[i]; };
+  for (int64_t i = 0; i < n_vox; ++i) if (is_hot(i) && has_nz(i)) order.push_back(i);
+  const int64_t n_hot_ne = (int64_t)order.size();
+  for (int64_t i = 0; i < n_vox; ++i) if (is_hot(i) && !has_nz(i)) order.push_back(i);
+  const int64_t n_hot = (int64_t)order.size();
+  for (int64_t i = 0; i < n_vox; ++i) if (!is_hot(i) && has_nz(i)) order.push_back(i);
+  const int64_t n_cold_ne = (int64_t)order.size() - n_hot;
+  for (int64_t i = 0; i < n_vox; ++i) if (!is_hot(i) && !has_nz(i)) order.push_back(i);
+  bool perm = false;
+  for (int64_t r = 0; r < n_vox && !perm; ++r) perm = order[r] != r;
   std::vector<int64_t> rp1;
-  if (roi) {
+  if (perm) {
     rp1.resize(n_vox + 1);
     rp1[0] = 0;
     for (int64_t r = 0; r < n_vox; ++r) rp1[r + 1] = rp1[r] + (rp0[order[r] + 1] - rp0[order[r]]);
   }
-  const std::vector<int64_t>& rpd = roi ? rp1 : rp0;
+  const std::vector<int64_t>& rpd = perm ? rp1 : rp0;
+  // every index / value array is zero padded past its last nonzero
+  const int64_t nnz_alloc = ((nnz + 255) & ~255LL) + kPadElems;
 
   // ---- upload + validate (on the input layout)
   DBuf<int64_t> rp_in;
@@ -556,9 +631,12 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   const float *Dp = D_val, *Lp = L_val;
   CK(upload_vec(h, rp_in, rp0));
   if (!dev_ptr(flags)) {
-    CK(col_in.alloc(nnz));
-    CK(D_in.alloc(nnz));
-    CK(L_in.alloc(nnz));
+    CK(col_in.alloc(nnz_alloc));
+    CK(D_in.alloc(nnz_alloc));
+    CK(L_in.alloc(nnz_alloc));
+    CK(cudaMemsetAsync(col_in.p + nnz, 0, (nnz_alloc - nnz) * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(D_in.p + nnz, 0, (nnz_alloc - nnz) * sizeof(float), s));
+    CK(cudaMemsetAsync(L_in.p + nnz, 0, (nnz_alloc - nnz) * sizeof(float), s));
     if (nnz) {
       CK(cudaMemcpyAsync(col_in.p, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
       CK(cudaMemcpyAsync(D_in.p, D_val, nnz * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -581,25 +659,25 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   h->rp.release(); h->col.release(); h->Dv.release(); h->Lv.release(); h->sD.release(); h->sL.release();
   h->voxel.release(); h->mask.release(); h->cp.release(); h->crow.release(); h->DTv.release(); h->LTv.release();
 
-  // ---- FP32 CSR in device order
+  // ---- FP32 CSR in device order (zero padded)
   DBuf<int32_t> col_d;
   DBuf<float> D_d, L_d;
   CK(upload_vec(h, h->rp, rpd));
-  if (roi) {
-    DBuf<int64_t> src_row;
-    CK(upload_vec(h, src_row, order));
-    CK(col_d.alloc(nnz));
-    CK(D_d.alloc(nnz));
-    CK(L_d.alloc(nnz));
-    launch_gather_rows(rp_in.p, src_row.p, h->rp.p, n_vox, colp, Dp, Lp, col_d.p, D_d.p, L_d.p, s);
-    CK(cudaGetLastError());
-    CK(upload_vec(h, h->voxel, order));
-    CK(cudaStreamSynchronize(s));
-  } else if (dev_ptr(flags)) {
-    CK(col_d.alloc(nnz));
-    CK(D_d.alloc(nnz));
-    CK(L_d.alloc(nnz));
-    if (nnz) {
+  if (perm || dev_ptr(flags)) {
+    CK(col_d.alloc(nnz_alloc));
+    CK(D_d.alloc(nnz_alloc));
+    CK(L_d.alloc(nnz_alloc));
+    CK(cudaMemsetAsync(col_d.p + nnz, 0, (nnz_alloc - nnz) * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(D_d.p + nnz, 0, (nnz_alloc - nnz) * sizeof(float), s));
+    CK(cudaMemsetAsync(L_d.p + nnz, 0, (nnz_alloc - nnz) * sizeof(float), s));
+    if (perm) {
+      DBuf<int64_t> src_row;
+      CK(upload_vec(h, src_row, order));
+      launch_gather_rows(rp_in.p, src_row.p, h->rp.p, n_vox, colp, Dp, Lp, col_d.p, D_d.p, L_d.p, s);
+      CK(cudaGetLastError());
+      CK(upload_vec(h, h->voxel, order));
+      CK(cudaStreamSynchronize(s));
+    } else if (nnz) {
       CK(cudaMemcpyAsync(col_d.p, col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(D_d.p, D_val, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(L_d.p, L_val, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -618,8 +696,10 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     h->Dv.p = reinterpret_cast<uint8_t*>(D_d.p); h->Dv.n = D_d.n * 4; D_d.p = nullptr; D_d.n = 0;
     h->Lv.p = reinterpret_cast<uint8_t*>(L_d.p); h->Lv.n = L_d.n * 4; L_d.p = nullptr; L_d.n = 0;
   } else {
-    CK(h->Dv.alloc((size_t)nnz * 2));
-    CK(h->Lv.alloc((size_t)nnz * 2));
+    CK(h->Dv.alloc((size_t)nnz_alloc * 2));
+    CK(h->Lv.alloc((size_t)nnz_alloc * 2));
+    CK(cudaMemsetAsync(h->Dv.p, 0, (size_t)nnz_alloc * 2, s));
+    CK(cudaMemsetAsync(h->Lv.p, 0, (size_t)nnz_alloc * 2, s));
     CK(h->sD.alloc(n_vox));
     CK(h->sL.alloc(n_vox));
     launch_quantize(fmt, h->rp.p, n_vox, D_d.p, L_d.p, h->Dv.p, h->Lv.p, h->sD.p, h->sL.p, s);
@@ -631,10 +711,11 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
 
   // ---- streamed rows: mask, FP64 moments
   h->V = n_vox; h->nnz = nnz; h->n = n_spots; h->n_pad = (n_spots + 3) & ~3;
-  h->fmt = fmt; h->roi = roi; h->n_hot = n_hot; h->nnz_hot = rpd[n_hot];
-  h->h_voxel = roi ? std::vector<int64_t>(order.begin(), order.end()) : std::vector<int64_t>();
+  h->fmt = fmt; h->roi = roi; h->perm = perm; h->n_hot = n_hot; h->nnz_hot = rpd[n_hot];
+  h->n_hot_ne = n_hot_ne; h->n_cold_ne = n_cold_ne;
+  h->h_voxel = perm ? std::vector<int64_t>(order.begin(), order.end()) : std::vector<int64_t>();
   h->h_mask.resize(n_hot);
-  for (int64_t r = 0; r < n_hot; ++r) h->h_mask[r] = m0[roi ? order[r] : r];
+  for (int64_t r = 0; r < n_hot; ++r) h->h_mask[r] = m0[order[r]];
   CK(upload_vec(h, h->mask, h->h_mask));
   CK(h->mdd.alloc(n_hot)); CK(h->mll.alloc(n_hot)); CK(h->mdl.alloc(n_hot));
   launch_moments(fmt, h->rp.p, n_hot, h->Dv.p, h->Lv.p, fmt ? h->sD.p : nullptr, fmt ? h->sL.p : nullptr,
@@ -663,9 +744,13 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(upload_vec(h, h->cp, cph));
     launch_csc_offsets(cnt.p, n_blk, n_spots, h->cp.p, s);
     const int vb = value_bytes(fmt);
-    CK(h->crow.alloc(h->nnz_hot));
-    CK(h->DTv.alloc((size_t)h->nnz_hot * vb));
-    CK(h->LTv.alloc((size_t)h->nnz_hot * vb));
+    const int64_t nh_alloc = ((h->nnz_hot + 255) & ~255LL) + kPadElems;
+    CK(h->crow.alloc(nh_alloc));
+    CK(h->DTv.alloc((size_t)nh_alloc * vb));
+    CK(h->LTv.alloc((size_t)nh_alloc * vb));
+    CK(cudaMemsetAsync(h->crow.p + h->nnz_hot, 0, (nh_alloc - h->nnz_hot) * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(h->DTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
+    CK(cudaMemsetAsync(h->LTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
     if (n_hot > 0)
       launch_csc_fill(fmt, h->rp.p, h->col.p, h->Dv.p, h->Lv.p, blk_d.p, n_blk, n_spots, cnt.p,
                       h->crow.p, h->DTv.p, h->LTv.p, s);
@@ -695,17 +780,21 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(cudaStreamSynchronize(s));
   }
 
-  // ---- row schedules of the forward product
+  // ---- row schedules of the forward product (rows with nonzeros only)
   {
-    std::vector<int64_t> wr = partition_rows(rpd, n_hot, h->geo.fwd_warps, 8);
+    std::vector<int64_t> wr = partition_pairs(rpd, {{0, n_hot_ne}}, h->geo.fwd_warps, 8);
     CK(upload_vec(h, h->warp_row_hot, wr));
-    std::vector<int64_t> wa = partition_rows(rpd, n_vox, h->geo.fwd_warps, 8);
+    std::vector<int64_t> wa =
+        partition_pairs(rpd, {{0, n_hot_ne}, {n_hot, n_hot + n_cold_ne}}, h->geo.fwd_warps, 8);
     CK(upload_vec(h, h->warp_row_all, wa));
     CK(cudaStreamSynchronize(s));
   }
   // streaming (evict-first) loads when the streamed matrices do not fit in L2
   const double mat_bytes = (double)h->nnz_hot * (4.0 + 2.0 * value_bytes(fmt));
-  h->hint_fwd = mat_bytes > 0.5 * (double)h->l2_bytes;
+#ifndef FO_STREAM_HINT
+#define FO_STREAM_HINT -1
+#endif
+  h->hint_fwd = FO_STREAM_HINT < 0 ? mat_bytes > 0.5 * (double)h->l2_bytes : FO_STREAM_HINT != 0;
   h->hint_bwd = h->hint_fwd;
 
   // ---- work buffers
@@ -715,7 +804,10 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   CK(cudaMemsetAsync(h->xbuf.p, 0, h->n_pad * sizeof(float), s));
   CK(cudaMemsetAsync(h->gtmp.p, 0, h->n_pad * sizeof(float), s));
   CK(h->yw.alloc(n_hot)); CK(h->yg.alloc(n_hot)); CK(h->r.alloc(n_hot)); CK(h->gam.alloc(n_hot));
+  // rows without nonzeros are never written by the forward product: keep them 0
+  CK(cudaMemsetAsync(h->yw.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
   CK(cudaMemsetAsync(h->yg.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
+  CK(cudaMemsetAsync(h->r.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
   CK(h->chunk_sum.alloc(h->n_chunks));
   const Geometry& G = h->geo;
   h->off_f = 0;
@@ -796,6 +888,13 @@ int fredopt_set_objective(fredopt_t h, int n, const fredopt_objective_term* t) {
     h->tab.obj[i].weight = t[i].weight;
     if (t[i].quantity == FREDOPT_Q_DOSE) h->obj_dose = true;
   }
+  if (h->begun) {
+    DeviceGuard dg(h->device);
+    h->st_host.f_empty = f_empty(h);
+    CK(cudaMemcpyAsync(&h->st.p->f_empty, &h->st_host.f_empty, sizeof(double), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   return FREDOPT_OK;
 }
 
@@ -850,6 +949,7 @@ int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
   d.norm = p.cimmino_norm;
   d.grad_normalize = p.grad_normalize ? 1 : 0;
   d.log_cap = p.log_capacity;
+  d.f_empty = f_empty(h);
   CK(cudaMemcpyAsync(h->st.p, &d, sizeof(DevState), cudaMemcpyHostToDevice, s));
   h->iters_run = 0;
   h->device_ms = 0.0;
@@ -930,6 +1030,9 @@ int fredopt_end(fredopt_t h, float* w_out, float* dose_out, float* letd_out, fre
       lptr = letd_out ? h->fout_b.p : nullptr;
     }
   }
+  CK(cudaMemsetAsync(h->y64.p, 0, std::max<int64_t>(1, h->V) * sizeof(double2), s));
+  if (dptr) CK(cudaMemsetAsync(dptr, 0, h->V * sizeof(float), s));
+  if (lptr) CK(cudaMemsetAsync(lptr, 0, h->V * sizeof(float), s));
   FwdArgs fa = fwd_args(h, false);
   fa.x = h->w.p;
   fa.y64 = h->y64.p;
@@ -1058,6 +1161,7 @@ int fredopt_forward(fredopt_t h, const float* w, float* dose_out, float* lw_out,
   rc = load_spot_vec(h, h->xbuf, w, flags);
   if (rc) return rc;
   CK(h->yall.ensure(std::max<int64_t>(1, h->V)));
+  CK(cudaMemsetAsync(h->yall.p, 0, std::max<int64_t>(1, h->V) * sizeof(float2), s));
   FwdArgs fa = fwd_args(h, false);
   fa.x = h->xbuf.p;
   fa.y = h->yall.p;
@@ -1069,7 +1173,7 @@ int fredopt_forward(fredopt_t h, const float* w, float* dose_out, float* lw_out,
     da = dose_out ? h->fout_a.p : nullptr;
     db = lw_out ? h->fout_b.p : nullptr;
   }
-  launch_scatter_y(h->yall.p, h->roi ? h->voxel.p : nullptr, h->V, da, db, s);
+  launch_scatter_y(h->yall.p, h->perm ? h->voxel.p : nullptr, h->V, da, db, s);
   CK(cudaGetLastError());
   if (!dev_ptr(flags)) {
     if (dose_out) CK(cudaMemcpyAsync(dose_out, h->fout_a.p, h->V * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -1096,7 +1200,7 @@ int fredopt_backward(fredopt_t h, const float* a_D, const float* a_L, float* u_o
     pa = a_D ? h->vin_a.p : nullptr;
     pb = a_L ? h->vin_b.p : nullptr;
   }
-  launch_scale_coef(h->n_hot, pa, pb, h->roi ? h->voxel.p : nullptr, h->fmt ? h->sD.p : nullptr,
+  launch_scale_coef(h->n_hot, pa, pb, h->perm ? h->voxel.p : nullptr, h->fmt ? h->sD.p : nullptr,
                     h->fmt ? h->sL.p : nullptr, h->gam.p, s);
   BwdArgs ba = bwd_args(h, h->gam.p);
   run(h, 1, [&] { launch_backward(h->geo, h->fmt, h->hint_bwd, true, ba, s); });
@@ -1180,7 +1284,7 @@ int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_ou
   collect_timers(h);
   if (rc) return rc;
   if (f_out) {
-    double f = 0.0;
+    double f = f_empty(h);
     for (double v : hp) f += v;
     *f_out = f;
   }
@@ -1204,7 +1308,7 @@ int fredopt_get_rows(fredopt_t h, int64_t* voxel, uint32_t* mask) {
   if (rc) return rc;
   DeviceGuard dg(h->device);
   if (voxel) {
-    if (h->roi) {
+    if (h->perm) {
       CK(cudaMemcpy(voxel, h->voxel.p, h->n_hot * sizeof(int64_t), cudaMemcpyDeviceToHost));
     } else {
       for (int64_t i = 0; i < h->n_hot; ++i) voxel[i] = i;

@@ -1,7 +1,9 @@
 // Internal declarations shared by the kernels and the C ABI of libfredopt.
-// Device data layout (all in HBM, device order of rows = "streamed rows"
-// first, then the rest; see fredopt_api.cu):
-//   CSR   rp int64[V+1], col int32[nnz], Dv/Lv VT[nnz], sD/sL float[V] (16-bit only)
+// Device data layout (all in HBM).  Device order of rows: streamed rows with
+// nonzeros, streamed rows without, other rows with nonzeros, other rows
+// without (each group ascending by voxel; see fredopt_api.cu):
+//   CSR   rp int64[V+1], col int32[nnz], Dv/Lv VT[nnz], sD/sL float[V] (16-bit only);
+//         col/D/L zero padded so whole 32*16-byte blocks past the end stay in bounds
 //   CSC   cp int64[n+1], row int32[nnz_hot] (index of a streamed row), DTv/LTv VT[nnz_hot]
 //   rows  voxel int64[V] (device row -> voxel), mask uint32[n_hot],
 //         FP64 moments |D_i|^2, |L_i|^2, <D_i,L_i> [n_hot]
@@ -16,6 +18,9 @@
 namespace fo {
 
 constexpr int kMaxCon = 32;
+// elements of zero padding after the last nonzero of every index/value array
+// (covers the block alignment and the prefetched unit of the streaming loop)
+constexpr int64_t kPadElems = 1024;
 constexpr int kMaxObj = 32;
 
 // constraint kinds (same numbering as the public header)
@@ -46,6 +51,7 @@ struct DevState {
   double coef;        // perturbed point x = w + coef * g
   double beta0, alpha, lam, eta, W_all;
   double f_start, f_cur, gnorm, beta_acc;
+  double f_empty;     // objective of streamed rows with no nonzeros (constant)
   long long k, s, accepted_total;
   int accepted;       // accepted steps in the current iteration
   int reductions, max_trials, norm, grad_normalize, log_cap;
@@ -72,7 +78,7 @@ struct FwdArgs {
   const void* Lv;
   const float* sD;       // row scales (16-bit storage) or null
   const float* sL;
-  const int64_t* warp_row;  // [n_warps + 1]
+  const int64_t* warp_row;  // [2 * n_warps]: row range [r0, r1) of each warp (nonempty rows)
   const float* x;
   int32_t n_x;           // number of spots
   int32_t n_x_pad;       // padded to a multiple of 4 (bulk-copy size)
@@ -144,7 +150,7 @@ struct ConArgs {
 
 struct Geometry {
   int n_sms;
-  int fwd_threads;      // 1024
+  int fwd_threads;      // 512
   int fwd_blocks;       // n_sms
   int fwd_warps;
   int bwd_threads;      // 256

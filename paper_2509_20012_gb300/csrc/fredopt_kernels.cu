@@ -29,7 +29,24 @@
 namespace fo {
 
 constexpr unsigned kFull = 0xffffffffu;
+// Launch shape and streaming depth (compile-time; the defaults were chosen
+// by measurement on GB300).
+#ifndef FO_FWD_UNROLL
+#define FO_FWD_UNROLL 2
+#endif
+#ifndef FO_BWD_UNROLL
+#define FO_BWD_UNROLL 2
+#endif
+#ifndef FO_PREFETCH_UNITS
+#define FO_PREFETCH_UNITS 1
+#endif
+#ifndef FO_BWD_MIN_BLOCKS
+#define FO_BWD_MIN_BLOCKS 4
+#endif
 constexpr int kFwdThreads = 1024;
+constexpr int kFwdUnroll = FO_FWD_UNROLL;
+constexpr int kBwdUnroll = FO_BWD_UNROLL;
+constexpr int kPrefetchUnits = FO_PREFETCH_UNITS;
 constexpr int kBwdThreads = 256;
 constexpr int kRowThreads = 256;
 constexpr int kColThreads = 256;
@@ -46,14 +63,47 @@ template <> struct VecOf<float> { static constexpr int V = 4; };
 template <> struct VecOf<__nv_bfloat16> { static constexpr int V = 8; };
 template <> struct VecOf<__half> { static constexpr int V = 8; };
 
+// 16-byte loads of the streamed arrays.  S = streaming (read once):
+// FO_LOAD_KIND 0: ld.global.cs (evict-first in L1 and L2);
+//              1: ld.global.L1::no_allocate;
+//              2: ld.global.L1::no_allocate with an L2 evict-first policy;
+//              3: ld.global.nc.L1::no_allocate.
+// Otherwise (data reused across passes while it fits in L2): ld.global.nc.
+#ifndef FO_LOAD_KIND
+#define FO_LOAD_KIND 0
+#endif
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ int4 ld_stream(const int4* p) {
+  int4 v;
+#if FO_LOAD_KIND == 0
+  v = __ldcs(p);
+#elif FO_LOAD_KIND == 1
+  asm volatile("ld.global.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+#elif FO_LOAD_KIND == 2
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(l2_evict_first_policy()));
+#else
+  asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+#endif
+  return v;
+}
 template <bool S>
 __device__ __forceinline__ int4 ld16(const int4* p) {
-  if (S) return __ldcs(p);
+  if (S) return ld_stream(p);
   return __ldg(p);
 }
 template <bool S>
 __device__ __forceinline__ uint4 ld16(const uint4* p) {
-  if (S) return __ldcs(p);
+  if (S) {
+    const int4 v = ld_stream(reinterpret_cast<const int4*>(p));
+    return make_uint4((unsigned)v.x, (unsigned)v.y, (unsigned)v.z, (unsigned)v.w);
+  }
   return __ldg(p);
 }
 
@@ -121,6 +171,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// bulk prefetch of [src, src + bytes) into L2 (TMA engine; no registers or
+// shared memory; bytes a multiple of 16, src 16-byte aligned)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // bounded wait on phase `parity`; true when the phase completed
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_spins) {
   const uint32_t a = smem_u32(bar);
@@ -136,74 +191,152 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int ma
   return false;
 }
 
-// ------------------------------------------------------------------ K1
+// ------------------------------------------------------------------ streaming core
 
-// One row: warp-wide dot products of the D and L rows with x (all lanes
-// return the totals).  Elements [s, e) of the shared index stream.
-template <typename VT, typename Acc, bool S>
-__device__ __forceinline__ void row_dot(const int32_t* __restrict__ col, const VT* __restrict__ Dv,
-                                        const VT* __restrict__ Lv, int64_t s, int64_t e,
-                                        const float* __restrict__ x, int lane, Acc& oD, Acc& oL) {
+// One 16-byte-per-lane block of the index stream and the two value streams.
+template <typename VT>
+struct Blk {
+  int4 c0, c1;  // indices (c1 only for 16-bit values: 8 per lane)
+  uint4 a, b;   // values of the two streams
+};
+
+template <typename VT, bool S, bool USE_A>
+__device__ __forceinline__ void load_blk(Blk<VT>& k, const int32_t* idx, const VT* Av, const VT* Bv,
+                                         int64_t p) {
   constexpr int V = VecOf<VT>::V;
-  int64_t a = (s + V - 1) & ~(int64_t)(V - 1);
-  if (a > e) a = e;
-  const int64_t ev = a + ((e - a) & ~(int64_t)(V - 1));
-  Acc d = 0, l = 0;
-  {
-    const int64_t p = s + lane;
-    if (p < a) {
-      const float xv = x[col[p]];
-      d += (Acc)to_f(Dv[p]) * (Acc)xv;
-      l += (Acc)to_f(Lv[p]) * (Acc)xv;
-    }
-  }
-  int64_t p = a + (int64_t)lane * V;
-  for (; p + 32 * V < ev; p += 64 * V) {
-    int c0[V], c1[V];
-    float d0[V], d1[V], l0[V], l1[V];
-    load_cols<V, S>(col + p, c0);
-    load_cols<V, S>(col + p + 32 * V, c1);
-    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
-    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p + 32 * V)), d1);
-    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
-    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p + 32 * V)), l1);
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const float xv = x[c0[q]];
-      d = fma((Acc)d0[q], (Acc)xv, d);
-      l = fma((Acc)l0[q], (Acc)xv, l);
-    }
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const float xv = x[c1[q]];
-      d = fma((Acc)d1[q], (Acc)xv, d);
-      l = fma((Acc)l1[q], (Acc)xv, l);
-    }
-  }
-  if (p < ev) {
-    int c0[V];
-    float d0[V], l0[V];
-    load_cols<V, S>(col + p, c0);
-    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
-    unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const float xv = x[c0[q]];
-      d = fma((Acc)d0[q], (Acc)xv, d);
-      l = fma((Acc)l0[q], (Acc)xv, l);
-    }
-  }
-  {
-    const int64_t t = ev + lane;
-    if (t < e) {
-      const float xv = x[col[t]];
-      d += (Acc)to_f(Dv[t]) * (Acc)xv;
-      l += (Acc)to_f(Lv[t]) * (Acc)xv;
-    }
-  }
-  oD = warp_sum(d);
-  oL = warp_sum(l);
+  k.c0 = ld16<S>(reinterpret_cast<const int4*>(idx + p));
+  if (V == 8) k.c1 = ld16<S>(reinterpret_cast<const int4*>(idx + p) + 1);
+  if (USE_A) k.a = ld16<S>(reinterpret_cast<const uint4*>(Av + p));
+  k.b = ld16<S>(reinterpret_cast<const uint4*>(Bv + p));
 }
+
+// Streams the elements [ptr[r0], ptr[r1]) of one warp as consecutive blocks
+// of 32*V elements (lane l holds elements l*V .. l*V+V-1 of a block; every
+// load is 16 bytes; the next unit of U blocks is in flight while the
+// current one is consumed) and splits the stream into the segments
+// [ptr[r], ptr[r+1]).  For element i with index c: sA += A_i * g(c).x and
+// sB += B_i * g(c).y.  A finished segment is summed over the warp in a fixed
+// butterfly; lane (r - base) keeps it; every 32 segments (and at the end)
+// flush(base, count, mine_A, mine_B) runs with lane j < count owning segment
+// base + j.  Deterministic: the split depends only on ptr, r0, r1.
+// The arrays must be readable (zero padded) up to
+// round_up(ptr[r1], 32*V) + U*32*V elements (a prefetch starts below ptr[r1]
+// and covers U*32*V elements, within the same bound).
+template <typename VT, typename Acc, bool S, bool USE_A, int U, class Gather, class Flush,
+          int PF = kPrefetchUnits, bool PP = false>
+__device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
+                                                const VT* __restrict__ Av, const VT* __restrict__ Bv,
+                                                const int64_t* __restrict__ ptr, int64_t r0, int64_t r1,
+                                                int lane, Gather gather, Flush flush) {
+  constexpr int V = VecOf<VT>::V;
+  constexpr int BLK = 32 * V;
+  constexpr int UB = U * BLK;
+  if (r0 >= r1) return;
+  // 32-bit offsets from the block-aligned start of the warp's range (a
+  // warp's range is far below 2^31 elements)
+  const int64_t start = ptr[r0] & ~(int64_t)(BLK - 1);
+  idx += start;
+  if (USE_A) Av += start;
+  Bv += start;
+  const int pb = (int)(ptr[r0] - start), pe = (int)(ptr[r1] - start);
+  const int nrows = (int)(r1 - r0);
+  int row = 0, base = 0;  // relative to r0
+  int ends = (lane < nrows) ? (int)(ptr[r0 + 1 + lane] - start) : pe;
+  int e_cur = __shfl_sync(kFull, ends, 0);
+  Acc sA = 0, sB = 0, myA = 0, myB = 0;
+  bool done = false;
+
+  // consume the U blocks of one unit starting at offset b
+  auto consume = [&](const Blk<VT>* unit, int b) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (done) return;
+      const int bb = b + u * BLK;
+      const int e0 = bb + lane * V;
+      int cs[V];
+      float av[V], bv[V];
+      cs[0] = unit[u].c0.x; cs[1] = unit[u].c0.y; cs[2] = unit[u].c0.z; cs[3] = unit[u].c0.w;
+      if (V == 8) { cs[4] = unit[u].c1.x; cs[5] = unit[u].c1.y; cs[6] = unit[u].c1.z; cs[7] = unit[u].c1.w; }
+      if (USE_A) unpack(VT(), unit[u].a, av);
+      unpack(VT(), unit[u].b, bv);
+      float2 gv[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) gv[q] = gather(cs[q]);
+      int lo = bb > pb ? bb : pb;
+      while (true) {
+        const int hi = e_cur < bb + BLK ? e_cur : bb + BLK;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const int e = e0 + q;
+          if (e >= lo && e < hi) {
+            if (USE_A) sA = fma((Acc)av[q], (Acc)gv[q].x, sA);
+            sB = fma((Acc)bv[q], (Acc)gv[q].y, sB);
+          }
+        }
+        if (e_cur > bb + BLK) break;  // the open segment continues in the next block
+        const Acc tA = warp_sum(sA), tB = warp_sum(sB);
+        sA = 0; sB = 0;
+        if (lane == row - base) { myA = tA; myB = tB; }
+        ++row;
+        if (row - base == 32 || row == nrows) {
+          flush(r0 + base, row - base, myA, myB);
+          myA = 0; myB = 0;
+          if (row == nrows) { done = true; return; }
+          base = row;
+          ends = (base + lane < nrows) ? (int)(ptr[r0 + base + 1 + lane] - start) : pe;
+        }
+        e_cur = __shfl_sync(kFull, ends, row - base);
+        lo = hi;
+        if (lo >= bb + BLK) break;
+      }
+    }
+  };
+  // lane 0 asks the TMA engine to bring the unit PF units ahead into L2, so
+  // the demand loads of the warp mostly wait on L2 rather than DRAM
+  auto prefetch_unit = [&](int q) {
+    if (PF > 0 && lane == 0 && q < pe) {
+      bulk_prefetch_l2(idx + q, (uint32_t)(UB * sizeof(int32_t)));
+      if (USE_A) bulk_prefetch_l2(Av + q, (uint32_t)(UB * sizeof(VT)));
+      bulk_prefetch_l2(Bv + q, (uint32_t)(UB * sizeof(VT)));
+    }
+  };
+  auto load_unit = [&](Blk<VT>* unit, int b) {
+    prefetch_unit(b + PF * UB);
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_blk<VT, S, USE_A>(unit[u], idx, Av, Bv, b + u * BLK + lane * V);
+  };
+
+  int b = 0;
+#pragma unroll
+  for (int k = 1; k < PF; ++k) prefetch_unit(b + k * UB);
+  if (PP) {
+    // ping-pong between two register units: while one is consumed the loads
+    // of the other are in flight (no register copies of pending loads)
+    Blk<VT> ua[U], ub[U];
+    load_unit(ua, b);
+    while (true) {
+      if (b + UB < pe) load_unit(ub, b + UB);
+      consume(ua, b);
+      if (done) break;
+      b += UB;
+      if (b + UB < pe) load_unit(ua, b + UB);
+      consume(ub, b);
+      if (done) break;
+      b += UB;
+    }
+  } else {
+    // one register unit: its U blocks are loaded together, then consumed;
+    // latency is hidden by the other warps of the SM
+    Blk<VT> ua[U];
+    while (!done) {
+      load_unit(ua, b);
+      consume(ua, b);
+      b += UB;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ K1
 
 // Objective of one row (Eq. 2 terms of the structures the voxel is in):
 // f_i = sum w (q - T)^2 ; residual rD = sum_DOSE 2w(Dx - T), rL = sum_CDL 2wc(cLx - T).
@@ -225,6 +358,7 @@ __device__ __forceinline__ void row_objective(const Tables& t, uint32_t m, doubl
   }
 }
 
+// Fused Dx, Lx over the warp's nonempty rows [warp_row[2w], warp_row[2w+1]).
 template <typename VT, int EPI, bool XS, bool S>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_forward(FwdArgs a, Tables t) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -253,61 +387,50 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_forward(FwdArgs a, Tables t)
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= a.n_warps) return;
-  const int64_t r0 = a.warp_row[warp], r1 = a.warp_row[warp + 1];
+  const int64_t r0 = a.warp_row[2 * warp], r1 = a.warp_row[2 * warp + 1];
   const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
   const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
   double acc0 = 0.0, acc1 = 0.0;  // per-lane partials of the epilogue reductions
-  for (int64_t base = r0; base < r1; base += 32) {
-    const int nr = (int)((r1 - base) < 32 ? (r1 - base) : 32);
-    int64_t ms = 0, me = 0;
-    if (lane < nr) {
-      ms = a.rp[base + lane];
-      me = a.rp[base + lane + 1];
-    }
-    Acc myD = 0, myL = 0;
-    unsigned todo = __ballot_sync(kFull, me > ms);
-    while (todo) {
-      const int j = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int64_t s = __shfl_sync(kFull, ms, j), e = __shfl_sync(kFull, me, j);
-      Acc dD, dL;
-      row_dot<VT, Acc, S>(a.col, Dv, Lv, s, e, x, lane, dD, dL);
-      if (lane == j) { myD = dD; myL = dL; }
-    }
-    if (lane < nr) {
-      const int64_t r = base + lane;
-      const double sd = a.sD ? (double)a.sD[r] : 1.0;
-      const double sl = a.sL ? (double)a.sL[r] : 1.0;
-      if (EPI == EPI_FINAL) {
-        const double Dx = (double)myD * sd, Lx = (double)myL * sl;
-        a.y64[r] = make_double2(Dx, Lx);
-        const int64_t v = a.voxel ? a.voxel[r] : r;
-        if (a.dose_out) a.dose_out[v] = (float)Dx;
-        if (a.letd_out) a.letd_out[v] = Dx > 0.0 ? (float)(Lx / Dx) : 0.0f;
-      } else {
-        const float Dx = (float)((double)myD * sd), Lx = (float)((double)myL * sl);
-        a.y[r] = make_float2(Dx, Lx);
-        if (EPI == EPI_OBJ) {
-          double f, rD, rL;
-          row_objective(t, a.mask[r], Dx, Lx, f, rD, rL);
-          a.r_out[r] = make_float2((float)(rD * sd), (float)(rL * sl));
-          acc0 += f;
-        } else if (EPI == EPI_BC) {
-          // B' = sum w (q(x) - T) q(g) = 1/2 (rD Dg + rL Lg); C' = sum w q(g)^2
-          const float2 rin = a.r_in[r];  // already multiplied by the row scales
-          acc0 += 0.5 * ((double)rin.x * (double)myD + (double)rin.y * (double)myL);
-          const uint32_t m = a.mask[r];
-          double PD = 0.0, PL = 0.0;
-          for (int i = 0; i < t.n_obj; ++i) {
-            if (!((m >> t.obj[i].bit) & 1u)) continue;
-            if (t.obj[i].q == 0) PD += t.obj[i].weight;
-            else PL += t.obj[i].weight;
-          }
-          acc1 += PD * (double)Dx * (double)Dx + PL * t.c * t.c * (double)Lx * (double)Lx;
+  auto gather = [&](int c) {
+    const float v = x[c];
+    return make_float2(v, v);
+  };
+  auto flush = [&](int64_t base, int cnt, Acc myD, Acc myL) {
+    if (lane >= cnt) return;
+    const int64_t r = base + lane;
+    const double sd = a.sD ? (double)a.sD[r] : 1.0;
+    const double sl = a.sL ? (double)a.sL[r] : 1.0;
+    if (EPI == EPI_FINAL) {
+      const double Dx = (double)myD * sd, Lx = (double)myL * sl;
+      a.y64[r] = make_double2(Dx, Lx);
+      const int64_t v = a.voxel ? a.voxel[r] : r;
+      if (a.dose_out) a.dose_out[v] = (float)Dx;
+      if (a.letd_out) a.letd_out[v] = Dx > 0.0 ? (float)(Lx / Dx) : 0.0f;
+    } else {
+      const float Dx = (float)((double)myD * sd), Lx = (float)((double)myL * sl);
+      a.y[r] = make_float2(Dx, Lx);
+      if (EPI == EPI_OBJ) {
+        double f, rD, rL;
+        row_objective(t, a.mask[r], Dx, Lx, f, rD, rL);
+        a.r_out[r] = make_float2((float)(rD * sd), (float)(rL * sl));
+        acc0 += f;
+      } else if (EPI == EPI_BC) {
+        // B' = sum w (q(x) - T) q(g) = 1/2 (rD Dg + rL Lg); C' = sum w q(g)^2
+        const float2 rin = a.r_in[r];  // already multiplied by the row scales
+        acc0 += 0.5 * ((double)rin.x * (double)myD + (double)rin.y * (double)myL);
+        const uint32_t m = a.mask[r];
+        double PD = 0.0, PL = 0.0;
+        for (int i = 0; i < t.n_obj; ++i) {
+          if (!((m >> t.obj[i].bit) & 1u)) continue;
+          if (t.obj[i].q == 0) PD += t.obj[i].weight;
+          else PL += t.obj[i].weight;
         }
+        acc1 += PD * (double)Dx * (double)Dx + PL * t.c * t.c * (double)Lx * (double)Lx;
       }
     }
-  }
+  };
+  stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : 1)>(a.col, Dv, Lv, a.rp, r0, r1, lane,
+                                                                          gather, flush);
   if (EPI == EPI_OBJ || EPI == EPI_BC) {
     acc0 = warp_sum(acc0);
     acc1 = warp_sum(acc1);
@@ -320,80 +443,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_forward(FwdArgs a, Tables t)
 
 // ------------------------------------------------------------------ K3
 
+// Chunk sums of the transposed product: chunk c = nonzeros [chunk_ptr[c],
+// chunk_ptr[c+1]) of one column; sum_i D_ij coef_i.x + L_ij coef_i.y.
 template <typename VT, bool S, bool UD>
-__global__ void __launch_bounds__(kBwdThreads) k_backward(BwdArgs a) {
-  constexpr int V = VecOf<VT>::V;
+__global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(BwdArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= a.n_warps) return;
   const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
   const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
-  const int32_t* __restrict__ row = a.row;
   const float2* __restrict__ cf = a.coef;
-  const int c1 = a.warp_chunk[warp + 1];
-  for (int c = a.warp_chunk[warp]; c < c1; ++c) {
-    const int64_t s = a.chunk_ptr[c], e = a.chunk_ptr[c + 1];
-    int64_t al = (s + V - 1) & ~(int64_t)(V - 1);
-    if (al > e) al = e;
-    const int64_t ev = al + ((e - al) & ~(int64_t)(V - 1));
-    float acc = 0.0f;
-    {
-      const int64_t p = s + lane;
-      if (p < al) {
-        const float2 g = __ldg(&cf[row[p]]);
-        if (UD) acc = fmaf(to_f(Dv[p]), g.x, acc);
-        acc = fmaf(to_f(Lv[p]), g.y, acc);
-      }
-    }
-    int64_t p = al + (int64_t)lane * V;
-    for (; p + 32 * V < ev; p += 64 * V) {
-      int r0[V], r1[V];
-      float d0[V], d1[V], l0[V], l1[V];
-      load_cols<V, S>(row + p, r0);
-      load_cols<V, S>(row + p + 32 * V, r1);
-      if (UD) {
-        unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
-        unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p + 32 * V)), d1);
-      }
-      unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
-      unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p + 32 * V)), l1);
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const float2 g = __ldg(&cf[r0[q]]);
-        if (UD) acc = fmaf(d0[q], g.x, acc);
-        acc = fmaf(l0[q], g.y, acc);
-      }
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const float2 g = __ldg(&cf[r1[q]]);
-        if (UD) acc = fmaf(d1[q], g.x, acc);
-        acc = fmaf(l1[q], g.y, acc);
-      }
-    }
-    if (p < ev) {
-      int r0[V];
-      float d0[V], l0[V];
-      load_cols<V, S>(row + p, r0);
-      if (UD) unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Dv + p)), d0);
-      unpack(VT(), ld16<S>(reinterpret_cast<const uint4*>(Lv + p)), l0);
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const float2 g = __ldg(&cf[r0[q]]);
-        if (UD) acc = fmaf(d0[q], g.x, acc);
-        acc = fmaf(l0[q], g.y, acc);
-      }
-    }
-    {
-      const int64_t t = ev + lane;
-      if (t < e) {
-        const float2 g = __ldg(&cf[row[t]]);
-        if (UD) acc = fmaf(to_f(Dv[t]), g.x, acc);
-        acc = fmaf(to_f(Lv[t]), g.y, acc);
-      }
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) a.chunk_sum[c] = acc;
-  }
+  auto gather = [&](int r) { return __ldg(&cf[r]); };
+  float* out = a.chunk_sum;
+  auto flush = [&](int64_t base, int cnt, float mA, float mB) {
+    if (lane < cnt) out[base + lane] = UD ? mA + mB : mB;
+  };
+  stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : 1)>(
+      a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[warp], a.warp_chunk[warp + 1], lane, gather, flush);
 }
 
 // ------------------------------------------------------------------ block reductions
@@ -583,7 +649,7 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
                                                 const double* part_bc, int nbc, const double* part_g,
                                                 int ng, DevState* st) {
   __shared__ double red[256];
-  const double f = block_sum_array(part_f, nf, red);
+  const double f = block_sum_array(part_f, nf, red) + (step == 0 ? st->f_empty : 0.0);
   const double Bp = block_sum_array(part_bc, nbc, red);
   const double Cp = block_sum_array(part_bc + nbc, nbc, red);
   const double gn2 = block_sum_array(part_g, ng, red);
@@ -971,8 +1037,11 @@ static void fwd_dispatch_epi(const Geometry& g, int epi, bool xs, bool st, const
   }
 }
 
+#ifndef FO_FWD_XS
+#define FO_FWD_XS 1
+#endif
 bool forward_uses_smem(const Geometry& g, int n_x_pad) {
-  return (size_t)n_x_pad * sizeof(float) + 16 <= g.smem_limit;
+  return FO_FWD_XS && (size_t)n_x_pad * sizeof(float) + 16 <= g.smem_limit;
 }
 
 void launch_forward(const Geometry& g, int fmt, int epi, bool stream_hint, const FwdArgs& a,

@@ -44,9 +44,11 @@ def abs_sum_bound(Mabs, xabs):
 
 
 def hot_rows(plan, rows):
-    if rows == "all":
-        return np.arange(plan.n_vox)
-    return np.nonzero(plan.mask)[0]
+    """Streamed rows in device order: rows with nonzeros, then rows without,
+    each ascending by voxel."""
+    hot = np.ones(plan.n_vox, bool) if rows == "all" else plan.mask != 0
+    nz = np.diff(plan.row_ptr) > 0
+    return np.concatenate([np.nonzero(hot & nz)[0], np.nonzero(hot & ~nz)[0]])
 
 
 # ---------------------------------------------------------------- setup (K5)
@@ -296,14 +298,19 @@ def test_quantized_storage(lib, tiny, fmt):
     pl, P, R = tiny
     with handle(lib, pl, fmt=fmt) as h:
         cp, row, DT, LT = h.get_csc()
+        vox, _ = h.get_rows()
         dose, lw = h.forward(pl.w0)
-    # the dequantised matrix, rebuilt from the exact CSC values
+    # the dequantised matrix, rebuilt from the exact CSC values (CSC rows are
+    # device rows; vox maps them to voxels)
     import scipy.sparse as sp
-    Dq = sp.csc_matrix((DT.astype(np.float64), row, cp), shape=(pl.n_vox, pl.n_spots))
-    Lq = sp.csc_matrix((LT.astype(np.float64), row, cp), shape=(pl.n_vox, pl.n_spots))
+    Dq = sp.csc_matrix((DT.astype(np.float64), vox[row], cp), shape=(pl.n_vox, pl.n_spots))
     d_ref = Dq @ pl.w0.astype(np.float64)
     np.testing.assert_array_less(np.abs(dose - d_ref), 1e-5 * np.abs(d_ref) + 1e-30)
-    rel_elem = np.abs(DT - P.D.tocsc().data.astype(np.float32)) / np.abs(P.D.tocsc().data)
+    # element-wise rounding of the stored values against the FP32 inputs, in device order
+    sub = P.D[vox]
+    cp32, row32, DT32 = oracle.transpose_csr(sub.indptr, sub.indices, pl.n_spots, sub.data.astype(np.float32))
+    np.testing.assert_array_equal(row32, row)
+    rel_elem = np.abs(DT.astype(np.float64) - DT32) / np.abs(DT32)
     assert rel_elem.max() <= (2.0 ** -8 if fmt == "bf16" else 2.0 ** -11) * 1.0001
     d32, _ = oracle.forward(P, pl.w0)
     err = np.max(np.abs(dose - d32)) / PRESC
