@@ -256,6 +256,37 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);
  * -1 for a null handle. */
 int64_t fredopt_launch_count(fredopt_t h);
 
+/* ---- transposed product without device allocation ----
+ *
+ * The paper has no counterpart: this is a service entry point of this
+ * library.  It computes u = D^T a_D + L^T a_L (the product of the
+ * projection and gradient steps) from a CSC matrix pair that the caller
+ * already holds in device memory, for callers that cannot allocate device
+ * memory where they need it (for example a host program whose own pool owns
+ * the GPU's memory, or a latency-critical loop that avoids cudaMalloc and
+ * cudaFree because they can synchronise the device).  It needs no handle
+ * and allocates nothing: its scratch is one fixed device array of 4.25 MiB
+ * inside the library, which every GPU that loads the library keeps until
+ * the process exits.
+ *
+ * Arguments (all pointers are device pointers on the current device):
+ * col_ptr int64[n_cols+1] (ascending, col_ptr[0] = 0, col_ptr[n_cols] = nnz),
+ * row int32[nnz] (row of each nonzero, 0 <= row < n_rows), D_val, L_val
+ * float[nnz]; a_D, a_L float[n_rows] (either may be NULL = zeros); u_out
+ * float[n_cols] (written).  The work is enqueued on `cuda_stream` (a
+ * cudaStream_t, NULL = the legacy default stream) and the call returns
+ * without waiting; synchronise the stream before reading u_out.
+ * Limits: 1 <= n_cols <= 65536 and nnz / 4096 + n_cols <= 1048576, otherwise
+ * FREDOPT_ERR_SHAPE.  Row indices outside [0, n_rows) are skipped and
+ * column pointers are clamped to [0, nnz], so malformed input cannot read
+ * outside the arrays.  The first call on a device looks up the scratch
+ * address for that device.  All calls share the one scratch array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  The result is deterministic. */
+int fredopt_backward_noalloc(int64_t n_rows, int32_t n_cols, int64_t nnz, const int64_t* col_ptr,
+                             const int32_t* row, const float* D_val, const float* L_val,
+                             const float* a_D, const float* a_L, float* u_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,10 @@ _SIGS = {
     "fredopt_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fredopt_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fredopt_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "fredopt_backward_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
 }
 
 
