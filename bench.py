@@ -45,6 +45,25 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, device=None) -> float:
+    """Maximum of a float over all ranks (identity without a process group)."""
+    try:
+        import torch.distributed as dist
+    except Exception:
+        return float(x)
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(steps_per_rank: int, max_ms: float, world: int) -> float:
+    """Iterations of all replicas per second of the slowest rank (weak scaling)."""
+    return world * steps_per_rank / (max_ms * 1e-3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -98,6 +117,14 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# DRAM bytes per nonzero of one forward launch (dram__bytes_read.sum +
+# dram__bytes_write.sum, ncu, half-resolution clinical phantom, average of the
+# two forward launches of an iteration); traffic grows with the nonzeros, so
+# it is scaled to the full plan.  FP32 storage only; the other storages have
+# no capture yet (null).
+FWD_TRAFFIC_PER_NNZ = {"fp32": 12.22}
 
 
 def fwd_bytes(nnz, rows, vb, n_launch_obj, n_launch_bc):
@@ -170,12 +197,7 @@ def run_gpu_arm(args):
         e1.record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(e0.elapsed_time(e1), device=f"cuda:{local}")
         kt = h.get_timing()
         launches = h.launch_count()
         w, dose, letd, rep = h.end()
@@ -199,6 +221,9 @@ def run_gpu_arm(args):
               "bytes_per_launch": bb / max(1, 2 * n_iter)}
         for r in (fw, bw):
             r["frac"] = r["achieved"] / hbm if r["achieved"] else None
+        t = FWD_TRAFFIC_PER_NNZ.get(fmt)
+        fw["traffic"] = t * sz["nnz_rows"] if t else None
+        bw["traffic"] = None
         return dict(ms=ms, kt=kt, launches=launches, clocks=clocks, rep=rep, sizes=sz, t_load=t_load,
                     fwd=fw, bwd=bw, w=w)
 
@@ -225,13 +250,8 @@ def run_gpu_arm(args):
         h.set_constraints(plan.constraints)
         h.set_objective(plan.objective)
         h.superiorize(pin_w0, args.e2e_iters, plan.alpha, plan.relaxation, outputs=(out_w, out_d, out_l))
-        t_e2e = time.perf_counter() - t0
+        t_e2e = reduce_max(time.perf_counter() - t0, device=f"cuda:{local}")
         h.close()
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([t_e2e], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
         h2d = sum(v.numel() * v.element_size() for v in pin.values()) + pin_mask.numel() * 4 + plan.n_spots * 4
         d2h = (plan.n_spots + 2 * plan.n_vox) * 4
         e2e = {"value": ws * args.e2e_iters / t_e2e, "unit": UNIT,
@@ -245,7 +265,7 @@ def run_gpu_arm(args):
 
     if rank == 0:
         dom = main["fwd"] if (main["fwd"]["ms_total"] or 0) >= (main["bwd"]["ms_total"] or 0) else main["bwd"]
-        value = ws * args.steps / (main["ms"] * 1e-3)
+        value = whole_job_value(args.steps, main["ms"], ws)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
@@ -257,8 +277,8 @@ def run_gpu_arm(args):
                            main["sizes"]["nnz"] * 12 / 1e9),
                        "parallelism": f"replicas{ws}", "generate_s": round(t_gen, 2),
                        "load_s": round(main["t_load"], 3)},
-            "roofline": {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac")} | {
-                "traffic": None, "kernel": dom["kernel"], "peak_source": hbm_src,
+            "roofline": {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")} | {
+                "kernel": dom["kernel"], "peak_source": hbm_src,
                 "forward": main["fwd"], "backward": main["bwd"]},
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -269,7 +289,7 @@ def run_gpu_arm(args):
                       "max_violation": main["rep"]["max_violation"]},
         }
         if roi is not None:
-            line["roi_rows"] = {"value": ws * args.steps / (roi["ms"] * 1e-3),
+            line["roi_rows"] = {"value": whole_job_value(args.steps, roi["ms"], ws),
                                 "ms_per_step": roi["ms"] / args.steps,
                                 "n_rows": roi["sizes"]["n_rows"], "nnz_rows": roi["sizes"]["nnz_rows"],
                                 "forward": roi["fwd"], "backward": roi["bwd"], "clocks": roi["clocks"],
