@@ -124,7 +124,7 @@ class ClockSampler:
 # two forward launches of an iteration); traffic grows with the nonzeros, so
 # it is scaled to the full plan.  FP32 storage only; the other storages have
 # no capture yet (null).
-FWD_TRAFFIC_PER_NNZ = {"fp32": 12.22}
+FWD_TRAFFIC_PER_NNZ = {"fp32": 12.17}
 
 
 def fwd_bytes(nnz, rows, vb, n_launch_obj, n_launch_bc):
@@ -202,6 +202,7 @@ def run_gpu_arm(args):
         launches = h.launch_count()
         w, dose, letd, rep = h.end()
         h.close()
+        log = None
         vb = 4 if fmt == "fp32" else 2
         nf = kt["forward"][1]
         nb = kt["backward"][1]
@@ -225,10 +226,39 @@ def run_gpu_arm(args):
         fw["traffic"] = t * sz["nnz_rows"] if t else None
         bw["traffic"] = None
         return dict(ms=ms, kt=kt, launches=launches, clocks=clocks, rep=rep, sizes=sz, t_load=t_load,
-                    fwd=fw, bwd=bw, w=w)
+                    fwd=fw, bwd=bw, w=w, dose=dose, letd=letd)
 
     main = timed_run("all")
     roi = timed_run("roi") if args.roi else None
+    prec = {}
+    if args.precision:
+        # FP64 reference outputs: the FP64-accumulated final pass of an FP32
+        # handle (the FP32 inputs multiplied in FP64)
+        ref = Handle(local, stream=stream)
+        ref.load_plan(plan)
+
+        def fp64_outputs(w):
+            ref.begin(w, plan.alpha, plan.relaxation)
+            _, d, l, _ = ref.end()
+            return d.astype(np.float64), l.astype(np.float64)
+
+        d32, l32 = fp64_outputs(main["w"])
+        for fmt in ("bf16", "fp16"):
+            r = timed_run("all", fmt)
+            d_ref, l_ref = fp64_outputs(r["w"])
+            sel = d_ref > 0.01 * plan.prescription
+            err_d = np.abs(r["dose"] - d_ref) / plan.prescription
+            err_l = np.abs(r["letd"] - l_ref)[sel]
+            prec[fmt] = {
+                "value": whole_job_value(args.steps, r["ms"], ws), "ms_per_step": r["ms"] / args.steps,
+                "forward": r["fwd"], "backward": r["bwd"],
+                "dose_err_max_frac_of_2Gy": float(err_d.max()), "dose_err_mean_frac_of_2Gy": float(err_d.mean()),
+                "letd_err_max_keV_um": float(err_l.max()), "letd_err_mean_keV_um": float(err_l.mean()),
+                "letd_err_where": "voxels with dose > 1% of prescription",
+                "vs_fp32_solution_dose_max_frac_of_2Gy": float(np.max(np.abs(d_ref - d32)) / plan.prescription),
+                "vs_fp32_solution_letd_max_keV_um": float(np.max(np.abs(l_ref - l32)[sel & (d32 > 0.01 * plan.prescription)])),
+            }
+        ref.close()
 
     # end to end: one plan re-optimisation from pinned host buffers through the C ABI
     e2e = None
@@ -288,6 +318,11 @@ def run_gpu_arm(args):
             "final": {"objective": main["rep"]["objective"], "n_violated": main["rep"]["n_violated"],
                       "max_violation": main["rep"]["max_violation"]},
         }
+        if prec:
+            line["precision"] = {"note": ("D and L stored in 16 bits with power-of-two FP32 row scales, "
+                                          "int32 indices, FP32 accumulation, FP64 norms and final check; "
+                                          "errors of the outputs at each run's final w against the FP64 "
+                                          "product of the FP32 inputs"), **prec}
         if roi is not None:
             line["roi_rows"] = {"value": whole_job_value(args.steps, roi["ms"], ws),
                                 "ms_per_step": roi["ms"] / args.steps,
@@ -358,6 +393,8 @@ def main():
     ap.add_argument("--no-roi", dest="roi", action="store_false")
     ap.add_argument("--e2e-iters", type=int, default=500)
     ap.add_argument("--cpu-iters", type=int, default=1)
+    ap.add_argument("--no-precision", dest="precision", action="store_false",
+                    help="skip the BF16/FP16 storage runs")
     ap.add_argument("--small", action="store_true",
                     help="half-resolution phantom (100x100x75 at 4 mm) for profiler captures")
     args = ap.parse_args()

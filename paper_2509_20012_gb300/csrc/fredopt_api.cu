@@ -780,12 +780,17 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(cudaStreamSynchronize(s));
   }
 
-  // ---- row schedules of the forward product (rows with nonzeros only)
+  // ---- row schedules of the forward product (rows with nonzeros only);
+  // a row end (two warp reductions and bookkeeping) costs about as much as
+  // streaming FO_ROW_COST nonzeros
+#ifndef FO_ROW_COST
+#define FO_ROW_COST 64
+#endif
   {
-    std::vector<int64_t> wr = partition_pairs(rpd, {{0, n_hot_ne}}, h->geo.fwd_warps, 8);
+    std::vector<int64_t> wr = partition_pairs(rpd, {{0, n_hot_ne}}, h->geo.fwd_warps, FO_ROW_COST);
     CK(upload_vec(h, h->warp_row_hot, wr));
     std::vector<int64_t> wa =
-        partition_pairs(rpd, {{0, n_hot_ne}, {n_hot, n_hot + n_cold_ne}}, h->geo.fwd_warps, 8);
+        partition_pairs(rpd, {{0, n_hot_ne}, {n_hot, n_hot + n_cold_ne}}, h->geo.fwd_warps, FO_ROW_COST);
     CK(upload_vec(h, h->warp_row_all, wa));
     CK(cudaStreamSynchronize(s));
   }

@@ -32,7 +32,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // Launch shape and streaming depth (compile-time; the defaults were chosen
 // by measurement on GB300).
 #ifndef FO_FWD_UNROLL
-#define FO_FWD_UNROLL 2
+#define FO_FWD_UNROLL 1
 #endif
 #ifndef FO_BWD_UNROLL
 #define FO_BWD_UNROLL 2
@@ -43,9 +43,20 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef FO_BWD_MIN_BLOCKS
 #define FO_BWD_MIN_BLOCKS 4
 #endif
-constexpr int kFwdThreads = 1024;
+#ifndef FO_FWD_XS
+#define FO_FWD_XS 1
+#endif
+#ifndef FO_FWD_THREADS
+#define FO_FWD_THREADS 1024
+#endif
+constexpr int kFwdThreads = FO_FWD_THREADS;
 constexpr int kFwdUnroll = FO_FWD_UNROLL;
 constexpr int kBwdUnroll = FO_BWD_UNROLL;
+#ifndef FO_UNROLL16
+#define FO_UNROLL16 2
+#endif
+constexpr int kFwdUnroll16 = FO_UNROLL16;
+constexpr int kBwdUnroll16 = FO_UNROLL16;
 constexpr int kPrefetchUnits = FO_PREFETCH_UNITS;
 constexpr int kBwdThreads = 256;
 constexpr int kRowThreads = 256;
@@ -60,8 +71,10 @@ __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 template <typename VT> struct VecOf;
 template <> struct VecOf<float> { static constexpr int V = 4; };
-template <> struct VecOf<__nv_bfloat16> { static constexpr int V = 8; };
-template <> struct VecOf<__half> { static constexpr int V = 8; };
+// 16-bit values: 4 per lane too (8-byte value loads), so a block keeps the
+// register footprint of the FP32 block and more blocks fit in a unit
+template <> struct VecOf<__nv_bfloat16> { static constexpr int V = 4; };
+template <> struct VecOf<__half> { static constexpr int V = 4; };
 
 // 16-byte loads of the streamed arrays.  S = streaming (read once):
 // FO_LOAD_KIND 0: ld.global.cs (evict-first in L1 and L2);
@@ -113,32 +126,23 @@ __device__ __forceinline__ void unpack(float, uint4 u, float* o) {
   o[2] = __uint_as_float(u.z);
   o[3] = __uint_as_float(u.w);
 }
+// 16-bit values: 4 per lane in the low 8 bytes (u.x, u.y)
 __device__ __forceinline__ void unpack(__nv_bfloat16, uint4 u, float* o) {
-  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+  const uint32_t w[2] = {u.x, u.y};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     o[2 * i] = __uint_as_float(w[i] << 16);
     o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
 }
 __device__ __forceinline__ void unpack(__half, uint4 u, float* o) {
-  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+  const uint32_t w[2] = {u.x, u.y};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     __half2 h = *reinterpret_cast<const __half2*>(&w[i]);
     float2 f = __half22float2(h);
     o[2 * i] = f.x;
     o[2 * i + 1] = f.y;
-  }
-}
-
-template <int V, bool S>
-__device__ __forceinline__ void load_cols(const int32_t* p, int* c) {
-  const int4 a = ld16<S>(reinterpret_cast<const int4*>(p));
-  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
-  if (V == 8) {
-    const int4 b = ld16<S>(reinterpret_cast<const int4*>(p) + 1);
-    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
   }
 }
 
@@ -196,18 +200,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int ma
 // One 16-byte-per-lane block of the index stream and the two value streams.
 template <typename VT>
 struct Blk {
-  int4 c0, c1;  // indices (c1 only for 16-bit values: 8 per lane)
-  uint4 a, b;   // values of the two streams
+  int4 c0;      // 4 indices
+  uint4 a, b;   // values of the two streams (16-bit: low 8 bytes)
 };
+
+template <bool S>
+__device__ __forceinline__ uint4 ld_vals(const float* p) {
+  return ld16<S>(reinterpret_cast<const uint4*>(p));
+}
+template <bool S, typename H>
+__device__ __forceinline__ uint4 ld_vals(const H* p) {  // 4 x 16-bit = 8 bytes
+  uint2 v;
+  if (S) v = __ldcs(reinterpret_cast<const uint2*>(p));
+  else v = __ldg(reinterpret_cast<const uint2*>(p));
+  return make_uint4(v.x, v.y, 0u, 0u);
+}
 
 template <typename VT, bool S, bool USE_A>
 __device__ __forceinline__ void load_blk(Blk<VT>& k, const int32_t* idx, const VT* Av, const VT* Bv,
                                          int64_t p) {
-  constexpr int V = VecOf<VT>::V;
   k.c0 = ld16<S>(reinterpret_cast<const int4*>(idx + p));
-  if (V == 8) k.c1 = ld16<S>(reinterpret_cast<const int4*>(idx + p) + 1);
-  if (USE_A) k.a = ld16<S>(reinterpret_cast<const uint4*>(Av + p));
-  k.b = ld16<S>(reinterpret_cast<const uint4*>(Bv + p));
+  if (USE_A) k.a = ld_vals<S>(Av + p);
+  k.b = ld_vals<S>(Bv + p);
 }
 
 // Streams the elements [ptr[r0], ptr[r1]) of one warp as consecutive blocks
@@ -256,7 +270,6 @@ __device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
       int cs[V];
       float av[V], bv[V];
       cs[0] = unit[u].c0.x; cs[1] = unit[u].c0.y; cs[2] = unit[u].c0.z; cs[3] = unit[u].c0.w;
-      if (V == 8) { cs[4] = unit[u].c1.x; cs[5] = unit[u].c1.y; cs[6] = unit[u].c1.z; cs[7] = unit[u].c1.w; }
       if (USE_A) unpack(VT(), unit[u].a, av);
       unpack(VT(), unit[u].b, bv);
       float2 gv[V];
@@ -360,7 +373,7 @@ __device__ __forceinline__ void row_objective(const Tables& t, uint32_t m, doubl
 
 // Fused Dx, Lx over the warp's nonempty rows [warp_row[2w], warp_row[2w+1]).
 template <typename VT, int EPI, bool XS, bool S>
-__global__ void __launch_bounds__(kFwdThreads, 1) k_forward(FwdArgs a, Tables t) {
+__global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(FwdArgs a, Tables t) {
   extern __shared__ __align__(128) unsigned char smem[];
   using Acc = typename std::conditional<EPI == EPI_FINAL, double, float>::type;
   const float* __restrict__ x = a.x;
@@ -429,7 +442,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_forward(FwdArgs a, Tables t)
       }
     }
   };
-  stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : 1)>(a.col, Dv, Lv, a.rp, r0, r1, lane,
+  stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : kFwdUnroll16)>(a.col, Dv, Lv, a.rp, r0, r1, lane,
                                                                           gather, flush);
   if (EPI == EPI_OBJ || EPI == EPI_BC) {
     acc0 = warp_sum(acc0);
@@ -458,7 +471,7 @@ __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(Bwd
   auto flush = [&](int64_t base, int cnt, float mA, float mB) {
     if (lane < cnt) out[base + lane] = UD ? mA + mB : mB;
   };
-  stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : 1)>(
+  stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16)>(
       a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[warp], a.warp_chunk[warp + 1], lane, gather, flush);
 }
 
@@ -1037,9 +1050,6 @@ static void fwd_dispatch_epi(const Geometry& g, int epi, bool xs, bool st, const
   }
 }
 
-#ifndef FO_FWD_XS
-#define FO_FWD_XS 1
-#endif
 bool forward_uses_smem(const Geometry& g, int n_x_pad) {
   return FO_FWD_XS && (size_t)n_x_pad * sizeof(float) + 16 <= g.smem_limit;
 }
@@ -1241,7 +1251,9 @@ int init_kernels(Geometry* g, int device) {
   g->n_sms = prop.multiProcessorCount;
   g->smem_limit = prop.sharedMemPerBlockOptin;
   g->fwd_threads = kFwdThreads;
-  g->fwd_blocks = g->n_sms;
+  // 1024 threads per SM: one CTA when x is staged in shared memory (120 KB
+  // for 30000 spots); smaller CTAs only when it is read through L1 instead
+  g->fwd_blocks = g->n_sms * (FO_FWD_XS ? 1 : 1024 / kFwdThreads);
   g->fwd_warps = g->fwd_blocks * (kFwdThreads / 32);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<float, true, true>, kBwdThreads, 0);

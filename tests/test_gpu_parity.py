@@ -423,3 +423,22 @@ def test_launch_count_and_timing(lib, tiny):
     assert t["constraints"][1] == 4
     assert n >= 8 * 4
     assert all(ms >= 0 for ms, c in t.values())
+
+
+def test_final_pass_is_fp64_product_of_fp32_inputs(lib, tiny):
+    """With FP32 storage the final pass (FP64 accumulation) equals the FP64
+    oracle product to FP64 rounding; bench.py uses it as the FP64 reference
+    of the 16-bit storage errors."""
+    pl, P, R = tiny
+    rng = np.random.default_rng(9)
+    w = rng.uniform(0.0, 2.0, pl.n_spots).astype(np.float32)
+    with handle(lib, pl) as h:
+        h.begin(w, pl.alpha, pl.relaxation)
+        w_out, dose, letd, rep = h.end()
+    np.testing.assert_array_equal(w_out, w)
+    d_ref, l_ref = oracle.forward(P, w)
+    lt_ref = oracle.letd(d_ref, l_ref)
+    np.testing.assert_allclose(dose, d_ref.astype(np.float32), rtol=2 ** -23, atol=0)
+    sel = d_ref > 0
+    np.testing.assert_allclose(letd[sel], lt_ref[sel].astype(np.float32), rtol=2 ** -22, atol=0)
+    assert np.all(letd[~sel] == 0)
