@@ -256,6 +256,77 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);
  * -1 for a null handle. */
 int64_t fredopt_launch_count(fredopt_t h);
 
+/* ---- serving: continuous batching of plan re-optimisations ----
+ *
+ * A server owns one device.  Requests (a whole plan plus its solve) are
+ * admitted first-in first-out while their estimated device footprint fits
+ * under `mem_cap_bytes` and fewer than `max_active` plans are loaded; each
+ * admitted plan stays resident on its own stream and its iterations are
+ * enqueued in rounds of `round_iters`, interleaved with the other active
+ * plans, so that their kernels overlap on the device.  A plan's results do
+ * not depend on its co-tenants (every tile shape depends on the plan alone):
+ * they are bit-identical to a fredopt_superiorize call on the same inputs.
+ * All request pointers are host pointers owned by the caller and must stay
+ * valid until the request is done (status DONE or an error).  Thread-safe. */
+typedef struct fredopt_request {
+  int64_t n_vox;
+  int64_t nnz;
+  int32_t n_spots;
+  int32_t format;                        /* as fredopt_load_influence */
+  const int64_t* row_ptr;                /* plan, as fredopt_load_influence */
+  const int32_t* col;
+  const float* D_val;
+  const float* L_val;
+  const uint32_t* voxel_mask;
+  int32_t n_constraints;
+  int32_t n_objective;
+  const fredopt_constraint* constraints;
+  const fredopt_objective_term* objective;
+  const float* w0;                       /* solve, as fredopt_superiorize */
+  int32_t iters;
+  int32_t pad;
+  double alpha;
+  double relaxation;
+  fredopt_params params;
+  float* w_out;                          /* outputs (float[n_spots], float[n_vox] x 2; may be NULL) */
+  float* dose_out;
+  float* letd_out;
+} fredopt_request;
+
+#define FREDOPT_QUEUED 0
+#define FREDOPT_LOADING 1
+#define FREDOPT_RUNNING 2
+#define FREDOPT_DONE 3
+
+typedef struct fredopt_ticket_info {
+  int32_t status;        /* FREDOPT_QUEUED .. FREDOPT_DONE, or a negative error code */
+  int32_t pad;
+  double t_submit;       /* seconds since the server was created */
+  double t_admit;        /* admitted (memory reserved), load starts */
+  double t_start;        /* loaded, iterations start */
+  double t_done;         /* outputs written */
+  int64_t footprint_bytes;
+  fredopt_report report; /* as fredopt_end */
+} fredopt_ticket_info;
+
+typedef struct fredopt_server* fredopt_server_t;
+
+/* Upper estimate of the device memory one plan needs while it loads and runs. */
+int64_t fredopt_footprint_bytes(int64_t n_vox, int32_t n_spots, int64_t nnz, int format);
+
+int fredopt_server_create(fredopt_server_t* out, int device, int64_t mem_cap_bytes, int max_active,
+                          int round_iters);
+/* Queue a request; FREDOPT_ERR_OOM if its footprint exceeds the cap. */
+int fredopt_server_submit(fredopt_server_t s, const fredopt_request* r, int64_t* ticket);
+int fredopt_server_poll(fredopt_server_t s, int64_t ticket, fredopt_ticket_info* info);
+/* Block until the request is done or `timeout_s` passes (FREDOPT_ERR_TIMEOUT). */
+int fredopt_server_wait(fredopt_server_t s, int64_t ticket, double timeout_s, fredopt_ticket_info* info);
+/* Block until every submitted request is done. */
+int fredopt_server_drain(fredopt_server_t s, double timeout_s);
+int fredopt_server_stats(fredopt_server_t s, int64_t* mem_used, int* n_active, int* n_queued);
+/* Finish the active plans, drop the queued ones and free the server. */
+int fredopt_server_destroy(fredopt_server_t s);
+
 /* ---- transposed product without device allocation ----
  *
  * The paper has no counterpart: this is a service entry point of this

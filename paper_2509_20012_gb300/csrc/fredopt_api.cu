@@ -1384,3 +1384,12 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches) {
 int64_t fredopt_launch_count(fredopt_t h) { return h ? h->launches : -1; }
 
 }  // extern "C"
+
+namespace fo {
+cudaStream_t handle_stream(fredopt_t h) { return h ? h->stream : nullptr; }
+int handle_device(fredopt_t h) { return h ? h->device : -1; }
+}  // namespace fo
+
+extern "C" {
+
+}  // extern "C"

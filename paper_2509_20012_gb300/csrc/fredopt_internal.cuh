@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+struct fredopt_ctx;
+
 namespace fo {
 
 constexpr int kMaxCon = 32;
@@ -214,5 +216,9 @@ void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_
                         cudaStream_t s);
 void launch_scale_coef(int64_t n, const float* aD, const float* aL, const int64_t* voxel,
                        const float* sD, const float* sL, float2* coef, cudaStream_t s);
+
+// handle internals used by the serving loop (fredopt_server.cu)
+cudaStream_t handle_stream(::fredopt_ctx* h);
+int handle_device(::fredopt_ctx* h);
 
 }  // namespace fo

@@ -72,6 +72,30 @@ class Report(ctypes.Structure):
         return d
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("n_vox", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_spots", ctypes.c_int32),
+                ("format", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("D_val", ctypes.c_void_p), ("L_val", ctypes.c_void_p), ("voxel_mask", ctypes.c_void_p),
+                ("n_constraints", ctypes.c_int32), ("n_objective", ctypes.c_int32),
+                ("constraints", ctypes.POINTER(Constraint)), ("objective", ctypes.POINTER(ObjectiveTerm)),
+                ("w0", ctypes.c_void_p), ("iters", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("relaxation", ctypes.c_double), ("params", Params),
+                ("w_out", ctypes.c_void_p), ("dose_out", ctypes.c_void_p), ("letd_out", ctypes.c_void_p)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("pad", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_int64), ("report", Report)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "report")}
+        d["report"] = self.report.as_dict()
+        return d
+
+
+QUEUED, LOADING, RUNNING, DONE = 0, 1, 2, 3
+
 _lib = None
 
 _SIGS = {
@@ -115,6 +139,17 @@ _SIGS = {
     "fredopt_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fredopt_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fredopt_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "fredopt_footprint_bytes": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int]),
+    "fredopt_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_int]),
+    "fredopt_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
+    "fredopt_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(TicketInfo)]),
+    "fredopt_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                           ctypes.POINTER(TicketInfo)]),
+    "fredopt_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "fredopt_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "fredopt_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fredopt_backward_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -386,3 +421,108 @@ class Handle:
 
     def launch_count(self) -> int:
         return int(self.lib.fredopt_launch_count(self.h))
+
+
+def footprint_bytes(n_vox, n_spots, nnz, fmt="fp32") -> int:
+    return int(load_library().fredopt_footprint_bytes(int(n_vox), int(n_spots), int(nnz), FORMATS[fmt]))
+
+
+class Server:
+    """Continuous-batching server on one GPU (fredopt_server_*).  Host arrays
+    of a request are kept referenced here until the request is done."""
+
+    def __init__(self, device: int = 0, mem_cap_bytes: float = 180e9, max_active: int = 8, round_iters: int = 10):
+        self.lib = load_library()
+        s = ctypes.c_void_p()
+        rc = self.lib.fredopt_server_create(ctypes.byref(s), device, int(mem_cap_bytes), max_active, round_iters)
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+        self.s = s
+        self._keep = {}
+
+    def submit(self, plan, fmt="fp32", rows="all", iters=None, alpha=None, relaxation=None, w0=None,
+               params: Params | None = None, **kw) -> int:
+        keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(x, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        r = Request()
+        r.n_vox = plan.n_vox
+        r.nnz = plan.nnz
+        r.n_spots = plan.n_spots
+        r.format = FORMATS[fmt] | ROWS[rows]
+        r.row_ptr = arr(plan.row_ptr, np.int64)
+        r.col = arr(plan.col, np.int32)
+        r.D_val = arr(plan.D, np.float32)
+        r.L_val = arr(plan.L, np.float32)
+        r.voxel_mask = arr(plan.mask, np.uint32)
+        con = (Constraint * max(1, len(plan.constraints)))()
+        for i, c in enumerate(plan.constraints):
+            con[i] = Constraint(int(c["struct_bit"]), KINDS[c["kind"]], float(c["bound"]), float(c["priority"]))
+        obj = (ObjectiveTerm * max(1, len(plan.objective)))()
+        for i, t in enumerate(plan.objective):
+            obj[i] = ObjectiveTerm(int(t["struct_bit"]), QUANTITIES[t["quantity"]], float(t["target"]),
+                                   float(t["weight"]))
+        keep += [con, obj]
+        r.n_constraints, r.n_objective = len(plan.constraints), len(plan.objective)
+        r.constraints, r.objective = con, obj
+        r.w0 = arr(plan.w0 if w0 is None else w0, np.float32)
+        r.iters = int(plan.iters if iters is None else iters)
+        r.alpha = float(plan.alpha if alpha is None else alpha)
+        r.relaxation = float(plan.relaxation if relaxation is None else relaxation)
+        r.params = params if params is not None else default_params(**kw)
+        out = (np.empty(plan.n_spots, np.float32), np.empty(plan.n_vox, np.float32), np.empty(plan.n_vox, np.float32))
+        keep += list(out)
+        r.w_out, r.dose_out, r.letd_out = (o.ctypes.data for o in out)
+        t = ctypes.c_int64()
+        rc = self.lib.fredopt_server_submit(self.s, ctypes.byref(r), ctypes.byref(t))
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+        self._keep[t.value] = (keep, out)
+        return t.value
+
+    def poll(self, ticket) -> dict:
+        info = TicketInfo()
+        rc = self.lib.fredopt_server_poll(self.s, ticket, ctypes.byref(info))
+        if rc != OK:
+            raise FredoptError(rc, "bad ticket")
+        return info.as_dict()
+
+    def wait(self, ticket, timeout=600.0):
+        """Returns (info, w, dose, letd) once the request is done (or failed)."""
+        info = TicketInfo()
+        rc = self.lib.fredopt_server_wait(self.s, ticket, float(timeout), ctypes.byref(info))
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+        keep, out = self._keep.pop(ticket)
+        return (info.as_dict(),) + tuple(out)
+
+    def drain(self, timeout=3600.0):
+        rc = self.lib.fredopt_server_drain(self.s, float(timeout))
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+
+    def stats(self):
+        m, a, q = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        self.lib.fredopt_server_stats(self.s, ctypes.byref(m), ctypes.byref(a), ctypes.byref(q))
+        return dict(mem_used=m.value, active=a.value, queued=q.value)
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.fredopt_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

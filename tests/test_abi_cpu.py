@@ -65,3 +65,30 @@ def test_null_and_bad_arguments_without_gpu(lib):
 def test_kernels_compiled_for_sm_103a():
     src = open(os.path.join(ROOT, "paper_2509_20012_gb300", "_build.py")).read()
     assert "arch=compute_103a,code=sm_103a" in src
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the public structs have the C sizes and offsets."""
+    import ctypes
+    import subprocess
+    from paper_2509_20012_gb300 import fredopt as f
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "fredopt.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fredopt_params), sizeof(fredopt_report),
+         sizeof(fredopt_request), sizeof(fredopt_ticket_info), sizeof(fredopt_log_entry),
+         sizeof(fredopt_constraint), sizeof(fredopt_objective_term), offsetof(fredopt_request, params),
+         offsetof(fredopt_request, w_out), offsetof(fredopt_request, alpha), offsetof(fredopt_ticket_info, report));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    c = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    py = [ctypes.sizeof(f.Params), ctypes.sizeof(f.Report), ctypes.sizeof(f.Request), ctypes.sizeof(f.TicketInfo),
+          ctypes.sizeof(f.LogEntry), ctypes.sizeof(f.Constraint), ctypes.sizeof(f.ObjectiveTerm),
+          f.Request.params.offset, f.Request.w_out.offset, f.Request.alpha.offset, f.TicketInfo.report.offset]
+    assert c == py
