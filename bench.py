@@ -289,6 +289,10 @@ def run_gpu_arm(args):
                "what": f"load_influence from pinned host + set_constraints + set_objective + "
                        f"superiorize({args.e2e_iters} iters) with host w0/w/dose/LETd; {t_e2e:.3f} s"}
 
+    serving = None
+    if ws == 1 and args.serve_requests > 0:
+        serving = serving_benchmark(args, local, clinical=None if args.small else plan)
+
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_iters > 0:
         cpu = cpu_baseline(plan, args.cpu_iters)
@@ -318,6 +322,8 @@ def run_gpu_arm(args):
             "final": {"objective": main["rep"]["objective"], "n_violated": main["rep"]["n_violated"],
                       "max_violation": main["rep"]["max_violation"]},
         }
+        if serving is not None:
+            line["serving"] = serving
         if prec:
             line["precision"] = {"note": ("D and L stored in 16 bits with power-of-two FP32 row scales, "
                                           "int32 indices, FP32 accumulation, FP64 norms and final check; "
@@ -334,6 +340,106 @@ def run_gpu_arm(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+SERVE_RES_MM = [8.0, 6.0, 5.0, 4.0, 3.0, 2.4, 2.0]  # clinical phantom family (2 mm = the clinical plan)
+
+
+def serving_library(clinical=None):
+    """Plans between the tiny plan and the clinical plan: the tiny plan and the
+    clinical phantom at 7 resolutions of the same geometry (`clinical`, the
+    2 mm plan, is reused when given)."""
+    import phantom
+    lib = [phantom.tiny_plan()]
+    for h in SERVE_RES_MM:
+        if h == 2.0 and clinical is not None:
+            lib.append(clinical)
+            continue
+        shape = (int(round(400 / h)), int(round(400 / h)), int(round(300 / h)))
+        lib.append(phantom.clinical_plan(shape=shape, h=h))
+    return lib
+
+
+def serving_trace(lib, n_req, rate, seed):
+    """Poisson arrivals (mean `rate`/s); sizes log-uniform between the smallest
+    and the largest plan (nearest plan of the library); FP32/BF16 50:50;
+    100-500 iterations."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    lognnz = np.log([p.nnz for p in lib])
+    target = rng.uniform(lognnz.min(), lognnz.max(), n_req)
+    idx = [int(np.argmin(np.abs(lognnz - x))) for x in target]
+    fmt = ["bf16" if u < 0.5 else "fp32" for u in rng.uniform(size=n_req)]
+    iters = rng.integers(100, 501, n_req)
+    return [dict(t=float(t[i]), plan=idx[i], fmt=fmt[i], iters=int(iters[i])) for i in range(n_req)]
+
+
+def run_trace(server, lib, trace, force_fp32=False, at_once=False):
+    import threading
+    tickets = [None] * len(trace)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, r in enumerate(trace):
+            d = t0 + r["t"] - time.perf_counter()
+            if d > 0 and not at_once:
+                time.sleep(d)
+            p = lib[r["plan"]]
+            tickets[i] = server.submit(p, fmt="fp32" if force_fp32 else r["fmt"], iters=r["iters"])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    return [server.wait(t, timeout=3600) for t in tickets]
+
+
+def serving_summary(results, n_req):
+    lat = np.array([r[0]["t_done"] - r[0]["t_submit"] for r in results])
+    span = max(r[0]["t_done"] for r in results) - min(r[0]["t_submit"] for r in results)
+    ok = all(r[0]["status"] == 3 for r in results)
+    return {"plans_per_hour": n_req / span * 3600.0, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+            "makespan_s": span, "all_done": ok}
+
+
+def serving_benchmark(args, local, clinical=None):
+    from paper_2509_20012_gb300 import Server
+    lib = serving_library(clinical)
+    trace = serving_trace(lib, args.serve_requests, args.serve_rate, args.seed + 1000)
+    with Server(local, mem_cap_bytes=180e9, max_active=8, round_iters=10) as srv:
+        served = run_trace(srv, lib, trace)
+    with Server(local, mem_cap_bytes=180e9, max_active=1, round_iters=10) as srv:
+        seq = run_trace(srv, lib, trace, force_fp32=True)
+    # capacity: the same requests all submitted at once (saturated queue)
+    with Server(local, mem_cap_bytes=180e9, max_active=8, round_iters=10) as srv:
+        cap_served = serving_summary(run_trace(srv, lib, trace, at_once=True), len(trace))
+    with Server(local, mem_cap_bytes=180e9, max_active=1, round_iters=10) as srv:
+        cap_seq = serving_summary(run_trace(srv, lib, trace, force_fp32=True, at_once=True), len(trace))
+    # accuracy of the mixed-precision results against the FP32 results of the same requests
+    dmax = lmax = 0.0
+    for r, a, b in zip(trace, served, seq):
+        if r["fmt"] == "fp32":
+            continue
+        p = lib[r["plan"]]
+        sel = b[2] > 0.01 * p.prescription
+        dmax = max(dmax, float(np.max(np.abs(a[2] - b[2]))) / p.prescription)
+        if sel.any():
+            lmax = max(lmax, float(np.max(np.abs(a[3] - b[3])[sel])))
+    sizes = [lib[r["plan"]].nnz for r in trace]
+    return {
+        "trace": (f"{args.serve_requests} requests, Poisson arrivals mean {args.serve_rate}/s, nnz per matrix "
+                  f"log-uniform {min(p.nnz for p in lib):.2e}-{max(p.nnz for p in lib):.2e} "
+                  f"(tiny plan + clinical phantom at {SERVE_RES_MM} mm), FP32/BF16 50:50, 100-500 iterations, "
+                  f"admission cap 180 GB"),
+        "requests_nnz_mean": float(np.mean(sizes)),
+        "served": serving_summary(served, len(trace)) | {"mode": "continuous batching, mixed FP32/BF16, "
+                                                                 "up to 8 plans resident"},
+        "sequential_fp32": serving_summary(seq, len(trace)) | {"mode": "one plan at a time, FP32"},
+        "capacity_plans_per_hour": {"served": cap_served["plans_per_hour"],
+                                    "sequential_fp32": cap_seq["plans_per_hour"],
+                                    "how": "the same requests submitted at once (saturated queue)"},
+        "bf16_vs_fp32_dose_max_frac_of_2Gy": dmax, "bf16_vs_fp32_letd_max_keV_um": lmax,
+    }
 
 
 def cpu_baseline(plan, iters):
@@ -393,6 +499,9 @@ def main():
     ap.add_argument("--no-roi", dest="roi", action="store_false")
     ap.add_argument("--e2e-iters", type=int, default=500)
     ap.add_argument("--cpu-iters", type=int, default=1)
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests of the serving trace (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="mean arrivals per second")
     ap.add_argument("--no-precision", dest="precision", action="store_false",
                     help="skip the BF16/FP16 storage runs")
     ap.add_argument("--small", action="store_true",

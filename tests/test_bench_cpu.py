@@ -52,3 +52,27 @@ def test_single_process_value():
     import bench
     assert bench.reduce_max(3.5) == 3.5
     assert bench.whole_job_value(500, 2500.0, 1) == pytest.approx(200.0)
+
+
+def test_bench_imports_and_serving_helpers():
+    """Everything bench.py imports exists; the serving trace is seeded and its
+    summary counts plans per hour and latency percentiles."""
+    import numpy as np
+    import bench
+    import paper_2509_20012_gb300 as pkg
+    for name in ("Handle", "Server", "default_params", "footprint_bytes", "DONE"):
+        assert hasattr(pkg, name)
+
+    class P:
+        def __init__(self, nnz):
+            self.nnz = nnz
+    lib = [P(3e6), P(3e7), P(5e8)]
+    t1 = bench.serving_trace(lib, 50, 2.0, seed=5)
+    t2 = bench.serving_trace(lib, 50, 2.0, seed=5)
+    assert t1 == t2
+    assert all(100 <= r["iters"] <= 500 and r["fmt"] in ("fp32", "bf16") for r in t1)
+    assert np.all(np.diff([r["t"] for r in t1]) > 0)
+    res = [({"t_submit": float(i), "t_done": float(i) + 1.0 + (i == 9), "status": 3},) for i in range(10)]
+    s = bench.serving_summary(res, 10)
+    assert s["all_done"] and s["p50_latency_s"] == 1.0 and s["makespan_s"] == 11.0
+    assert s["plans_per_hour"] == 10 / 11.0 * 3600
