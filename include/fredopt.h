@@ -256,6 +256,39 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);
  * -1 for a null handle. */
 int64_t fredopt_launch_count(fredopt_t h);
 
+/* ---- tile autotuning and batches of plans ----
+ *
+ * Tiles are the contiguous ranges of rows (forward product) and of column
+ * chunks (transposed product) that each warp streams.  They are balanced by
+ * nonzeros plus a weight per row end / per chunk.  A segment's sum does not
+ * depend on which warp streams it, so the weights change speed, never a
+ * result bit.  fredopt_autotune times the forward and transposed products
+ * with `reps` repetitions for each candidate weight (rows: 16..512, chunks:
+ * 4..1024) and keeps the fastest pair; it may be called after load or after
+ * begin.  fredopt_get_tuning reports the weights in use. */
+int fredopt_autotune(fredopt_t h, int reps, int64_t* row_cost, int64_t* chunk_cost);
+int fredopt_get_tuning(fredopt_t h, int64_t* row_cost, int64_t* chunk_cost);
+
+/* A batch runs the iterations of several begun plans (distinct handles and
+ * streams, one device, timing off) as one CUDA graph per iteration whose
+ * branches are the plans, so plans of uneven sizes run concurrently from a
+ * single launch.  Each plan's results are bit-identical to running it alone.
+ * Create after fredopt_begin on every handle (preferably with use_graphs = 0);
+ * then fredopt_batch_iterate (asynchronous), fredopt_batch_sync (waits and
+ * returns the device time of the iterate calls), fredopt_end per handle. */
+typedef struct fredopt_batch* fredopt_batch_t;
+int fredopt_batch_create(fredopt_batch_t* out, const fredopt_t* handles, int n);
+int fredopt_batch_iterate(fredopt_batch_t b, int iters);
+int fredopt_batch_sync(fredopt_batch_t b, double* device_ms);
+int fredopt_batch_destroy(fredopt_batch_t b);
+
+/* begin + batch iterate + end for n plans in one call; arrays of n pointers
+ * (output arrays and reps may be NULL). */
+int fredopt_superiorize_batch(const fredopt_t* handles, int n, const float* const* w0, int iters, double alpha,
+                              double relaxation, const fredopt_params* params, float* const* w_out,
+                              float* const* dose_out, float* const* letd_out, fredopt_report* reps,
+                              uint32_t flags);
+
 /* ---- serving: continuous batching of plan re-optimisations ----
  *
  * A server owns one device.  Requests (a whole plan plus its solve) are

@@ -3,6 +3,6 @@
 the C ABI of include/fredopt.h); `fredopt` is its argument-marshalling
 binding."""
 from .fredopt import (  # noqa: F401
-    DEVICE_PTR, DONE, FORMATS, KINDS, NORMS, QUANTITIES, ROWS, FredoptError, Handle, Params, Server,
-    default_params, footprint_bytes, load_library,
+    Batch, DEVICE_PTR, DONE, FORMATS, KINDS, NORMS, QUANTITIES, ROWS, FredoptError, Handle, Params, Server,
+    default_params, footprint_bytes, load_library, superiorize_batch,
 )

@@ -85,6 +85,9 @@ struct fredopt_ctx {
   int64_t n_chunks = 0;
   bool hint_fwd = true, hint_bwd = true;
   std::vector<int64_t> h_voxel;  // device row -> voxel (host copy, when perm)
+  std::vector<int64_t> h_rp;     // row_ptr in device order (host copy, for the schedules)
+  std::vector<int64_t> h_cptr;   // chunk_ptr (host copy)
+  int64_t row_cost = 0, chunk_cost = 0;  // warp-partition weights in use
   std::vector<uint32_t> h_mask;  // per streamed row
 
   // problem
@@ -437,6 +440,29 @@ void enqueue_iteration(fredopt_t h) {
   run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
 }
 
+// Warp partitions.  A segment's sum does not depend on which warp streams it
+// (lanes take elements by their absolute block-aligned position and add them
+// in order), so these weights change the speed, never a result bit.
+int set_fwd_schedule(fredopt_t h, int64_t row_cost) {
+  const std::vector<int64_t> wr = partition_pairs(h->h_rp, {{0, h->n_hot_ne}}, h->geo.fwd_warps, row_cost);
+  const std::vector<int64_t> wa = partition_pairs(
+      h->h_rp, {{0, h->n_hot_ne}, {h->n_hot, h->n_hot + h->n_cold_ne}}, h->geo.fwd_warps, row_cost);
+  CK(cudaMemcpyAsync(h->warp_row_hot.p, wr.data(), wr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->warp_row_all.p, wa.data(), wa.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->row_cost = row_cost;
+  return FREDOPT_OK;
+}
+
+int set_bwd_schedule(fredopt_t h, int64_t chunk_cost) {
+  const std::vector<int64_t> w64 = partition_rows(h->h_cptr, h->n_chunks, h->geo.bwd_warps, chunk_cost);
+  const std::vector<int32_t> w32(w64.begin(), w64.end());
+  CK(cudaMemcpyAsync(h->warp_chunk.p, w32.data(), w32.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->chunk_cost = chunk_cost;
+  return FREDOPT_OK;
+}
+
 // Objective (Eq. 2 terms) of the streamed rows without nonzeros: their dose
 // and LET-weighted dose are 0 for every w, so each term contributes w*T^2.
 double f_empty(fredopt_t h) {
@@ -580,6 +606,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   free_graph(h);
   h->loaded = false;
   h->begun = false;
+  int rc = FREDOPT_OK;
   cudaStream_t s = h->stream;
   join_in(h);
 
@@ -772,28 +799,28 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     cchunk[n_spots] = (int32_t)cptr.size();
     h->n_chunks = (int64_t)cptr.size();
     cptr.push_back(h->nnz_hot);
-    std::vector<int64_t> wch64 = partition_rows(cptr, h->n_chunks, W3, 16);
-    std::vector<int32_t> wch(wch64.begin(), wch64.end());
     CK(upload_vec(h, h->chunk_ptr, cptr));
     CK(upload_vec(h, h->col_chunk, cchunk));
-    CK(upload_vec(h, h->warp_chunk, wch));
     CK(cudaStreamSynchronize(s));
+    h->h_cptr.swap(cptr);
+    CK(h->warp_chunk.alloc(W3 + 1));
+    rc = set_bwd_schedule(h, 16);
+    if (rc) return rc;
   }
 
   // ---- row schedules of the forward product (rows with nonzeros only);
   // a row end (two warp reductions and bookkeeping) costs about as much as
-  // streaming FO_ROW_COST nonzeros
+  // streaming FO_ROW_COST nonzeros (fredopt_autotune can pick another weight)
 #ifndef FO_ROW_COST
 #define FO_ROW_COST 64
 #endif
-  {
-    std::vector<int64_t> wr = partition_pairs(rpd, {{0, n_hot_ne}}, h->geo.fwd_warps, FO_ROW_COST);
-    CK(upload_vec(h, h->warp_row_hot, wr));
-    std::vector<int64_t> wa =
-        partition_pairs(rpd, {{0, n_hot_ne}, {n_hot, n_hot + n_cold_ne}}, h->geo.fwd_warps, FO_ROW_COST);
-    CK(upload_vec(h, h->warp_row_all, wa));
-    CK(cudaStreamSynchronize(s));
-  }
+  h->h_rp = rpd;
+  h->n_hot_ne = n_hot_ne;
+  h->n_cold_ne = n_cold_ne;
+  CK(h->warp_row_hot.alloc(2 * (size_t)h->geo.fwd_warps));
+  CK(h->warp_row_all.alloc(2 * (size_t)h->geo.fwd_warps));
+  rc = set_fwd_schedule(h, FO_ROW_COST);
+  if (rc) return rc;
   // streaming (evict-first) loads when the streamed matrices do not fit in L2
   const double mat_bytes = (double)h->nnz_hot * (4.0 + 2.0 * value_bytes(fmt));
 #ifndef FO_STREAM_HINT
@@ -1382,6 +1409,248 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches) {
 }
 
 int64_t fredopt_launch_count(fredopt_t h) { return h ? h->launches : -1; }
+
+int fredopt_get_tuning(fredopt_t h, int64_t* row_cost, int64_t* chunk_cost) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (row_cost) *row_cost = h->row_cost;
+  if (chunk_cost) *chunk_cost = h->chunk_cost;
+  return FREDOPT_OK;
+}
+
+int fredopt_autotune(fredopt_t h, int reps, int64_t* row_cost, int64_t* chunk_cost) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (reps < 1 || h->timing) return fail(h, FREDOPT_ERR_INVALID_ARG, "reps >= 1, timing off");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  const Geometry& G = h->geo;
+  // inputs: w of the solve if one is begun, else ones; coefficients 1
+  if (!h->begun) {
+    std::vector<float> ones(h->n, 1.0f);
+    CK(cudaMemcpyAsync(h->xbuf.p, ones.data(), h->n * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  const float* x = h->begun ? h->w.p : h->xbuf.p;
+  launch_scale_coef(h->n_hot, nullptr, nullptr, nullptr, nullptr, nullptr, h->gam.p, s);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_ms = [&](auto&& launch) -> float {
+    launch();  // warm-up
+    float best = 1e30f;
+    for (int i = 0; i < reps; ++i) {
+      cudaEventRecord(e0, s);
+      launch();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  FwdArgs fa = fwd_args(h, true);
+  fa.x = x;
+  fa.y = h->yw.p;
+  int64_t best_row = h->row_cost;
+  float best_f = 1e30f;
+  for (int64_t c : {16, 32, 64, 128, 256, 512}) {
+    if ((rc = set_fwd_schedule(h, c))) break;
+    const float t = time_ms([&] { launch_forward(G, h->fmt, EPI_STORE, h->hint_fwd, fa, h->tab, s); });
+    if (t < best_f) { best_f = t; best_row = c; }
+  }
+  BwdArgs ba = bwd_args(h, h->gam.p);
+  int64_t best_chunk = h->chunk_cost;
+  float best_b = 1e30f;
+  for (int64_t c : {4, 16, 64, 256, 1024}) {
+    if (rc || (rc = set_bwd_schedule(h, c))) break;
+    const float t = time_ms([&] { launch_backward(G, h->fmt, h->hint_bwd, true, ba, s); });
+    if (t < best_b) { best_b = t; best_chunk = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if ((rc = set_fwd_schedule(h, best_row))) return rc;
+  if ((rc = set_bwd_schedule(h, best_chunk))) return rc;
+  rc = check_sticky(h);
+  if (rc) return rc;
+  if (row_cost) *row_cost = best_row;
+  if (chunk_cost) *chunk_cost = best_chunk;
+  return FREDOPT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct fredopt_batch {
+  int device = 0;
+  cudaStream_t root = nullptr;
+  std::vector<fredopt_t> hs;
+  std::vector<int> nodes;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
+  std::vector<cudaEvent_t> joins;
+  double ms = 0.0;
+  bool pending = false;
+};
+
+namespace {
+void batch_free(fredopt_batch* b) {
+  if (b->root) cudaStreamSynchronize(b->root);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  for (cudaEvent_t e : {b->fork, b->done, b->t0, b->t1})
+    if (e) cudaEventDestroy(e);
+  if (b->root) cudaStreamDestroy(b->root);
+  delete b;
+}
+}  // namespace
+
+extern "C" {
+
+int fredopt_batch_create(fredopt_batch_t* out, const fredopt_t* handles, int n) {
+  if (!out || !handles || n < 1) return FREDOPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int dev = handles[0] ? handles[0]->device : -1;
+  for (int i = 0; i < n; ++i) {
+    fredopt_t h = handles[i];
+    if (!h || !h->loaded || !h->begun || h->device != dev || h->timing) return FREDOPT_ERR_NOT_LOADED;
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == h || handles[j]->stream == h->stream) return FREDOPT_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(dev);
+  fredopt_batch* b = new fredopt_batch();
+  b->device = dev;
+  b->hs.assign(handles, handles + n);
+  auto bad = [&](cudaError_t e) {
+    batch_free(b);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FREDOPT_ERR_OOM : FREDOPT_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+  for (cudaEvent_t* ev : {&b->fork, &b->done})
+    if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+  if ((e = cudaEventCreate(&b->t0)) != cudaSuccess || (e = cudaEventCreate(&b->t1)) != cudaSuccess) return bad(e);
+  b->joins.resize(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    if ((e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+    if ((e = cudaStreamSynchronize(handles[i]->stream)) != cudaSuccess) return bad(e);
+  }
+  // one iteration of every plan as parallel branches of one graph
+  if ((e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return bad(e);
+  cudaEventRecord(b->fork, b->root);
+  for (int i = 0; i < n; ++i) {
+    fredopt_t h = handles[i];
+    cudaStreamWaitEvent(h->stream, b->fork, 0);
+    const int64_t before = h->launches;
+    enqueue_iteration(h);
+    b->nodes.push_back((int)(h->launches - before));
+    h->launches = before;
+    cudaEventRecord(b->joins[i], h->stream);
+    cudaStreamWaitEvent(b->root, b->joins[i], 0);
+  }
+  e = cudaStreamEndCapture(b->root, &b->graph);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return bad(e);
+  }
+  if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return bad(e);
+  *out = b;
+  return FREDOPT_OK;
+}
+
+int fredopt_batch_iterate(fredopt_batch_t b, int iters) {
+  if (!b || iters < 0) return FREDOPT_ERR_INVALID_ARG;
+  if (iters == 0) return FREDOPT_OK;
+  DeviceGuard dg(b->device);
+  if (b->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(b->t1);
+    if (cudaEventElapsedTime(&ms, b->t0, b->t1) == cudaSuccess) b->ms += ms;
+    b->pending = false;
+  }
+  for (fredopt_t h : b->hs) {  // order after any work the caller queued on the plans
+    cudaEventRecord(h->ev_join, h->stream);
+    cudaStreamWaitEvent(b->root, h->ev_join, 0);
+  }
+  cudaEventRecord(b->t0, b->root);
+  for (int i = 0; i < iters; ++i)
+    if (cudaGraphLaunch(b->exec, b->root) != cudaSuccess) {
+      cudaGetLastError();
+      return FREDOPT_ERR_CUDA;
+    }
+  cudaEventRecord(b->t1, b->root);
+  b->pending = true;
+  cudaEventRecord(b->done, b->root);
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    fredopt_t h = b->hs[i];
+    cudaStreamWaitEvent(h->stream, b->done, 0);  // later calls on the plan see the iterations
+    h->iters_run += iters;
+    h->launches += (int64_t)iters * b->nodes[i];
+  }
+  return FREDOPT_OK;
+}
+
+int fredopt_batch_sync(fredopt_batch_t b, double* device_ms) {
+  if (!b) return FREDOPT_ERR_INVALID_ARG;
+  DeviceGuard dg(b->device);
+  if (cudaStreamSynchronize(b->root) != cudaSuccess) {
+    cudaGetLastError();
+    return FREDOPT_ERR_CUDA;
+  }
+  if (b->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->t0, b->t1) == cudaSuccess) b->ms += ms;
+    b->pending = false;
+  }
+  if (device_ms) *device_ms = b->ms;
+  for (fredopt_t h : b->hs) {
+    int err = 0;
+    cudaMemcpy(&err, &h->st.p->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) return FREDOPT_ERR_TIMEOUT;
+  }
+  return FREDOPT_OK;
+}
+
+int fredopt_batch_destroy(fredopt_batch_t b) {
+  if (!b) return FREDOPT_ERR_INVALID_ARG;
+  DeviceGuard dg(b->device);
+  batch_free(b);
+  return FREDOPT_OK;
+}
+
+int fredopt_superiorize_batch(const fredopt_t* handles, int n, const float* const* w0, int iters, double alpha,
+                              double relaxation, const fredopt_params* params, float* const* w_out,
+                              float* const* dose_out, float* const* letd_out, fredopt_report* reps,
+                              uint32_t flags) {
+  if (!handles || !w0 || n < 1) return FREDOPT_ERR_INVALID_ARG;
+  fredopt_params p;
+  if (params) p = *params;
+  else fredopt_default_params(&p);
+  p.use_graphs = 0;  // the batch graph replaces the per-plan graphs
+  for (int i = 0; i < n; ++i) {
+    const int rc = fredopt_begin(handles[i], w0[i], alpha, relaxation, &p, flags);
+    if (rc) return rc;
+  }
+  fredopt_batch_t b = nullptr;
+  int rc = fredopt_batch_create(&b, handles, n);
+  if (rc) return rc;
+  rc = fredopt_batch_iterate(b, iters);
+  if (!rc) rc = fredopt_batch_sync(b, nullptr);
+  fredopt_batch_destroy(b);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    rc = fredopt_end(handles[i], w_out ? w_out[i] : nullptr, dose_out ? dose_out[i] : nullptr,
+                     letd_out ? letd_out[i] : nullptr, reps ? &reps[i] : nullptr, flags);
+    if (rc) return rc;
+  }
+  return FREDOPT_OK;
+}
 
 }  // extern "C"
 

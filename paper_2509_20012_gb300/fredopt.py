@@ -150,6 +150,21 @@ _SIGS = {
     "fredopt_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "fredopt_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fredopt_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "fredopt_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "fredopt_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.c_int]),
+    "fredopt_batch_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "fredopt_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "fredopt_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fredopt_superiorize_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.POINTER(Params),
+                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Report),
+                                                 ctypes.c_uint32]),
     "fredopt_backward_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -422,6 +437,17 @@ class Handle:
     def launch_count(self) -> int:
         return int(self.lib.fredopt_launch_count(self.h))
 
+    def autotune(self, reps: int = 3):
+        """Time candidate tile weights and keep the fastest (results unchanged)."""
+        r, c = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.fredopt_autotune(self.h, int(reps), ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
+
+    def tuning(self):
+        r, c = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.fredopt_get_tuning(self.h, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
+
 
 def footprint_bytes(n_vox, n_spots, nnz, fmt="fp32") -> int:
     return int(load_library().fredopt_footprint_bytes(int(n_vox), int(n_spots), int(nnz), FORMATS[fmt]))
@@ -526,3 +552,67 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Iterations of several begun plans as one CUDA graph per iteration
+    (fredopt_batch_*)."""
+
+    def __init__(self, handles):
+        self.lib = load_library()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.h for h in self.handles])
+        b = ctypes.c_void_p()
+        rc = self.lib.fredopt_batch_create(ctypes.byref(b), arr, len(self.handles))
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+        self.b = b
+
+    def iterate(self, iters: int):
+        rc = self.lib.fredopt_batch_iterate(self.b, int(iters))
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+
+    def sync(self) -> float:
+        ms = ctypes.c_double()
+        rc = self.lib.fredopt_batch_sync(self.b, ctypes.byref(ms))
+        if rc != OK:
+            raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
+        return ms.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fredopt_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def superiorize_batch(handles, w0s, iters, alpha, relaxation, params: Params | None = None, **kw):
+    """fredopt_superiorize_batch with host arrays; returns [(w, dose, letd, report)]."""
+    lib = load_library()
+    n = len(handles)
+    if params is None:
+        params = default_params(**kw)
+    hs = (ctypes.c_void_p * n)(*[h.h for h in handles])
+    w0a = [np.ascontiguousarray(w, np.float32) for w in w0s]
+    outs = [(np.empty(h.n_spots, np.float32), np.empty(h.n_vox, np.float32), np.empty(h.n_vox, np.float32))
+            for h in handles]
+    ptr = lambda xs: (ctypes.c_void_p * n)(*[x.ctypes.data for x in xs])
+    reps = (Report * n)()
+    rc = lib.fredopt_superiorize_batch(hs, n, ptr(w0a), int(iters), float(alpha), float(relaxation),
+                                       ctypes.byref(params), ptr([o[0] for o in outs]), ptr([o[1] for o in outs]),
+                                       ptr([o[2] for o in outs]), reps, 0)
+    if rc != OK:
+        raise FredoptError(rc, lib.fredopt_strerror(rc).decode())
+    return [o + (reps[i].as_dict(),) for i, o in enumerate(outs)]
