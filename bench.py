@@ -442,6 +442,85 @@ def serving_benchmark(args, local, clinical=None):
     }
 
 
+def batching_benchmark(args, local):
+    """SURVEY cfg3: (a) 16 independent plans, PTV 20-400 cc, nnz 6e5-7e7,
+    BF16, tiles autotuned per plan, run one after another vs as one batch
+    graph per iteration; (b) 27 robustness scenarios stacked into one robust
+    plan (one w meets the constraints in every scenario), BF16."""
+    import phantom
+    from paper_2509_20012_gb300 import Batch, Handle
+    iters = args.batch_iters
+    plans = phantom.batch_plans(16, seed=args.seed)
+    # one after another: each plan alone
+    seq_ms, seq_w, tiles = 0.0, [], []
+    for p in plans:
+        with Handle(local) as h:
+            h.load_plan(p, fmt="bf16")
+            tiles.append(h.autotune(reps=3))
+            h.begin(p.w0, p.alpha, p.relaxation)
+            h.iterate(iters)
+            w, d, l, rep = h.end()
+            seq_ms += rep["device_ms"]
+            seq_w.append(w)
+    # all plans as one graph per iteration
+    hs = []
+    for p in plans:
+        h = Handle(local)
+        h.load_plan(p, fmt="bf16")
+        h.autotune(reps=3)
+        h.begin(p.w0, p.alpha, p.relaxation, use_graphs=0)
+        hs.append(h)
+    with Batch(hs) as b:
+        b.iterate(3)       # warm-up, then the timed iterations continue the same solves
+        b.sync()
+        t0 = b.sync()
+        b.iterate(iters - 3)
+        bat_ms = b.sync() - t0
+    same = True
+    for h, w_ref in zip(hs, seq_w):
+        w, *_ = h.end()
+        same = same and bool(np.array_equal(w, w_ref))
+        h.close()
+    total_iters = iters * len(plans)
+    out = {"independent": {
+        "plans": len(plans), "nnz_per_matrix": [int(p.nnz) for p in plans], "storage": "bf16",
+        "iterations_per_plan": iters, "tiles_row_chunk_weight": tiles,
+        "sequential_plan_iters_per_s": total_iters / (seq_ms * 1e-3),
+        "batched_plan_iters_per_s": (iters - 3) * len(plans) / (bat_ms * 1e-3),
+        "batch_graph_results_identical_to_sequential": same}}
+    out["independent"]["batched_speedup"] = (out["independent"]["batched_plan_iters_per_s"]
+                                             / out["independent"]["sequential_plan_iters_per_s"])
+    if args.robust:
+        t = time.perf_counter()
+        rp, per = phantom.robust_plan(seed=args.seed)
+        t_gen = time.perf_counter() - t
+        with Handle(local) as h:
+            t = time.perf_counter()
+            h.load_plan(rp, fmt="bf16")
+            t_load = time.perf_counter() - t
+            tune = h.autotune(reps=2)
+            h.set_timing(True)
+            h.begin(rp.w0, rp.alpha, rp.relaxation)
+            h.iterate(3)
+            h.get_timing()
+            h.set_timing(True)
+            h.iterate(iters)
+            kt = h.get_timing()
+            w, d, l, rep = h.end()
+        ms = sum(v[0] for v in kt.values())
+        hbm, _ = peaks()
+        fb = kt["forward"][0]
+        f_bytes = 2 * iters * (rp.nnz * 8 + int(np.count_nonzero(np.diff(rp.row_ptr) > 0)) * 36)
+        out["robust_stacked"] = {
+            "scenarios": len(per), "nnz_per_scenario_matrix": int(np.mean(per)), "nnz_stacked": int(rp.nnz),
+            "rows_stacked": int(rp.n_vox), "n_spots": int(rp.n_spots), "storage": "bf16", "tiles": tune,
+            "iters_per_s": iters / (ms * 1e-3), "forward_GBps": f_bytes / (fb * 1e-3) / 1e9,
+            "forward_frac_of_hbm": f_bytes / (fb * 1e-3) / 1e9 / hbm,
+            "generate_s": round(t_gen, 1), "load_s": round(t_load, 2),
+            "final_max_violation": rep["max_violation"], "final_objective": rep["objective"]}
+    return out
+
+
 def cpu_baseline(plan, iters):
     """FP64 oracle, as it stands, on `iters` iterations of the same plan."""
     import oracle
@@ -506,7 +585,18 @@ def main():
                     help="skip the BF16/FP16 storage runs")
     ap.add_argument("--small", action="store_true",
                     help="half-resolution phantom (100x100x75 at 4 mm) for profiler captures")
+    ap.add_argument("--batching", action="store_true",
+                    help="run the batching workloads (16 independent plans; 27 stacked robustness scenarios)")
+    ap.add_argument("--no-robust", dest="robust", action="store_false")
+    ap.add_argument("--batch-iters", type=int, default=100)
     args = ap.parse_args()
+    if args.batching:
+        import torch
+        ws, rank, local = dist_env()
+        torch.cuda.set_device(local)
+        res = batching_benchmark(args, local)
+        print(json.dumps({"metric": "batching (SURVEY cfg3)", "n_gpus": 1, "data": "synthetic", **res}))
+        return
     if args.warmup < 3:
         args.warmup = 3
     # the reference arm (FP64 oracle on the host cores) is bounded: one

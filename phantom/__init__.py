@@ -350,3 +350,103 @@ def random_csr(n_rows: int, n_cols: int, density: float, seed: int, let_range=(0
     let = rng.uniform(let_range[0], let_range[1], size=col.shape[0])
     L = (let * D).astype(np.float32)
     return row_ptr, col, D, L
+
+
+# ----------------------------------------------------------------- batching workloads
+
+ROBUST_SHAPE = (120, 120, 100)
+ROBUST_H = 2.5
+
+
+def _sphere_plan(name, shape, h, ptv_r_mm, angles, spots, layers, pitch, seed, noise, shift_mm=(0.0, 0.0, 0.0),
+                 density_scale=1.0, iters=100, layer_mm=3.0):
+    """Water phantom with a spherical PTV at the centre and a distal OAR
+    cylinder (behind the first field), spots on a lateral grid and layers
+    `layer_mm` apart in range spanning the PTV along each field."""
+    nx, ny, nz = shape
+    iso = [0.5 * nx * h, 0.5 * ny * h, 0.5 * nz * h]
+    span = layer_mm * (layers - 1)
+    first, last = [], []
+    for ang in angles:
+        d_iso = {0.0: iso[2], 90.0: iso[0], 270.0: nx * h - iso[0], 180.0: nz * h - iso[2]}[ang]
+        first.append(d_iso - 0.5 * span)
+        last.append(d_iso + 0.5 * span)
+    p = make_params(nx=nx, ny=ny, nz=nz, h_mm=h, n_fields=len(angles), angle_deg=list(angles), iso_mm=iso,
+                    spots_x=spots, spots_y=spots, spot_pitch_mm=pitch, n_layers=layers, range_first_mm=first,
+                    range_last_mm=last, sigma_mm=4.0, trunc_rel=1e-4, noise_rel=noise, seed=seed,
+                    shift_mm=list(shift_mm), density_scale=density_scale, dose_at_iso=2.0)
+    row_ptr, col, D, L = generate(p)
+    x, y, z = voxel_centres_mm(nx, ny, nz, h)
+    X, Y, Z = x - iso[0], y - iso[1], z - iso[2]
+    ptv = X ** 2 + Y ** 2 + Z ** 2 <= ptv_r_mm ** 2
+    oar = (X ** 2 + (Z - (ptv_r_mm + 12.0)) ** 2 <= 10.0 ** 2) & (np.abs(Y) <= 2 * ptv_r_mm)
+    mask = ptv.astype(np.uint32) | (oar.astype(np.uint32) << 1)
+    structures = [dict(name="PTV", bit=0, role="target"), dict(name="OAR", bit=1, role="oar")]
+    constraints = [dict(struct_bit=0, kind="DOSE_MIN", bound=0.95 * 2.0, priority=1.0),
+                   dict(struct_bit=0, kind="DOSE_MAX", bound=1.07 * 2.0, priority=1.0),
+                   dict(struct_bit=1, kind="DOSE_MAX", bound=1.2, priority=1.0),
+                   dict(struct_bit=1, kind="LETD_MAX", bound=2.5, priority=1.0)]
+    n = int(p.n_fields * p.n_layers * p.spots_x * p.spots_y)
+    return Plan(name=name, shape=tuple(shape), h_mm=h, params=p, row_ptr=row_ptr, col=col, D=D, L=L, mask=mask,
+                structures=structures, constraints=constraints,
+                objective=default_objective(structures, constraints), w0=np.ones(n, np.float32), iters=iters,
+                alpha=0.99, relaxation=1.0)
+
+
+def batch_plans(n_plans: int = 16, seed: int = 0):
+    """Independent plans with PTV volumes log-spaced 20-400 cc in the
+    300 x 300 x 250 mm phantom: spots 6 mm apart over the PTV plus 12 mm,
+    layers 4 mm apart in range over the PTV depth plus 12 mm, one field below
+    150 cc, else two; voxels from 5 mm (smallest PTV) to 3 mm (largest)."""
+    plans = []
+    vols = np.geomspace(20.0, 400.0, n_plans)
+    for i, v in enumerate(vols):
+        r = (3.0 * v * 1000.0 / (4.0 * np.pi)) ** (1.0 / 3.0)
+        frac = i / max(1, n_plans - 1)
+        h = float(np.exp(np.log(5.0) + frac * (np.log(3.0) - np.log(5.0))))
+        shape = tuple(int(round(s * ROBUST_H / h)) for s in ROBUST_SHAPE)
+        angles = [0.0] if v < 150 else [0.0, 90.0]
+        spots = int(np.ceil((2 * r + 12.0) / 6.0))
+        layers = int(np.ceil((2 * r + 12.0) / 4.0))
+        plans.append(_sphere_plan(f"ptv{v:.0f}cc", shape, h, r, angles, spots, layers, 6.0, seed + i, 0.01,
+                                  layer_mm=4.0))
+    return plans
+
+
+def robust_scenarios():
+    """27 scenarios: setup shift x in {-3, 0, +3} mm x setup shift y in
+    {-3, 0, +3} mm x range (water-equivalent depth) scaled by {0.965, 1, 1.035};
+    the shift along the first beam's axis is carried by the range factor."""
+    return [((sx, sy, 0.0), rs) for sx in (-3.0, 0.0, 3.0) for sy in (-3.0, 0.0, 3.0)
+            for rs in (0.965, 1.0, 1.035)]
+
+
+def robust_plan(seed: int = 0, noise: float = 0.01, scenarios=None):
+    """Robust plan on the 120x120x100 phantom at 2.5 mm (two fields at 0 and
+    90 degrees, 2 x 64 x 64 spots ... trimmed to 8192 spots: 16 x 16 lateral x
+    16 layers per field): the rows of every scenario's influence matrices are
+    stacked, so one spot-weight vector has to meet the constraints in all
+    scenarios (structure masks follow the patient).  Returns (plan, nnz per
+    scenario)."""
+    scen = robust_scenarios() if scenarios is None else scenarios
+    parts, per = [], []
+    for k, (shift, rs) in enumerate(scen):
+        pl = _sphere_plan("robust", ROBUST_SHAPE, ROBUST_H, 25.0, [0.0, 90.0], 16, 16, 4.0, seed, noise,
+                          shift_mm=shift, density_scale=rs)
+        parts.append(pl)
+        per.append(pl.nnz)
+    base = parts[0]
+    V = base.n_vox
+    row_ptr = np.zeros(V * len(parts) + 1, np.int64)
+    off = 0
+    for k, pl in enumerate(parts):
+        row_ptr[1 + k * V:1 + (k + 1) * V] = pl.row_ptr[1:] + off
+        off += pl.nnz
+    col = np.concatenate([pl.col for pl in parts])
+    D = np.concatenate([pl.D for pl in parts])
+    L = np.concatenate([pl.L for pl in parts])
+    mask = np.tile(base.mask, len(parts))
+    plan = Plan(name="robust27", shape=(V * len(parts), 1, 1), h_mm=ROBUST_H, params=base.params, row_ptr=row_ptr,
+                col=col, D=D, L=L, mask=mask, structures=base.structures, constraints=base.constraints,
+                objective=base.objective, w0=base.w0.copy(), iters=100, alpha=0.99, relaxation=1.0)
+    return plan, per
