@@ -292,6 +292,9 @@ def run_gpu_arm(args):
     serving = None
     if ws == 1 and args.serve_requests > 0:
         serving = serving_benchmark(args, local, clinical=None if args.small else plan)
+    batching = None
+    if ws == 1 and args.batch:
+        batching = batching_benchmark(args, local)
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_iters > 0:
@@ -324,6 +327,8 @@ def run_gpu_arm(args):
         }
         if serving is not None:
             line["serving"] = serving
+        if batching is not None:
+            line["batching"] = batching
         if prec:
             line["precision"] = {"note": ("D and L stored in 16 bits with power-of-two FP32 row scales, "
                                           "int32 indices, FP32 accumulation, FP64 norms and final check; "
@@ -586,7 +591,9 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="half-resolution phantom (100x100x75 at 4 mm) for profiler captures")
     ap.add_argument("--batching", action="store_true",
-                    help="run the batching workloads (16 independent plans; 27 stacked robustness scenarios)")
+                    help="run only the batching workloads (16 independent plans; 27 stacked robustness scenarios)")
+    ap.add_argument("--no-batch", dest="batch", action="store_false",
+                    help="skip the batching workloads in the default run")
     ap.add_argument("--no-robust", dest="robust", action="store_false")
     ap.add_argument("--batch-iters", type=int, default=100)
     args = ap.parse_args()
