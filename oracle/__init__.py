@@ -9,3 +9,7 @@ from .fredopt_oracle import (  # noqa: F401
     objective_gradient, cimmino_step, sequential_ams_sweep, superiorize, transpose_csr,
     final_report,
 )
+from .volume import (  # noqa: F401
+    QUANTITIES, at_volume_rank, coverage, cumulative_volume, derive_cdl_limits, quantity,
+    structure_voxels, value_at_volume, volume_histogram,
+)
