@@ -289,6 +289,10 @@ def run_gpu_arm(args):
                "what": f"load_influence from pinned host + set_constraints + set_objective + "
                        f"superiorize({args.e2e_iters} iters) with host w0/w/dose/LETd; {t_e2e:.3f} s"}
 
+    volume = None
+    if rank == 0 and args.volume:
+        volume = volume_benchmark(plan, main["w"], local, stream, hbm)
+
     serving = None
     if ws == 1 and args.serve_requests > 0:
         serving = serving_benchmark(args, local, clinical=None if args.small else plan)
@@ -325,6 +329,8 @@ def run_gpu_arm(args):
             "final": {"objective": main["rep"]["objective"], "n_violated": main["rep"]["n_violated"],
                       "max_violation": main["rep"]["max_violation"]},
         }
+        if volume is not None:
+            line["volume_stats"] = volume
         if serving is not None:
             line["serving"] = serving
         if batching is not None:
@@ -526,6 +532,53 @@ def batching_benchmark(args, local):
     return out
 
 
+def volume_benchmark(plan, w, local, stream, hbm, reps=20):
+    """Volume statistics of the final fluence (Sec. 2.4.1): 1000-bin DVH,
+    cDLVH and LVH of every structure, and the values at volume a plan review
+    reads (PTV D98/D95/D50/D2, OAR cDL30 and D2), timed by class with CUDA
+    events on the library stream."""
+    from paper_2509_20012_gb300 import Handle
+    h = Handle(local, stream=stream)
+    h.load_plan(plan)
+    bits = sorted({s["bit"] for s in plan.structures})
+    oars = [s["bit"] for s in plan.structures if s["role"] == "oar"]
+    ptv = [s["bit"] for s in plan.structures if s["role"] == "target"][0]
+    top = {"DOSE": 1.3 * plan.prescription, "CDL": 0.5, "LETD": 15.0}
+    hist = [{"quantity": q, "struct_bit": b, "edges": np.linspace(0.0, top[q], 1001, dtype=np.float32)}
+            for b in bits for q in ("DOSE", "CDL", "LETD")]
+    sel = ([{"quantity": "DOSE", "struct_bit": ptv, "fracs": [0.98, 0.95, 0.5, 0.02]}] +
+           [{"quantity": "CDL", "struct_bit": b, "fracs": [0.30]} for b in oars] +
+           [{"quantity": "DOSE", "struct_bit": b, "fracs": [0.02]} for b in oars])
+    out = {}
+    any_bits = np.uint32(sum(1 << b for b in bits))
+    n_struct = int(np.count_nonzero(plan.mask & any_bits))
+    for name, reqs, n_pass in (("histograms", hist, 1), ("values_at_volume", sel, 5)):
+        for _ in range(3):
+            res = h.volume_stats(reqs, w)
+        h.set_timing(True)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            res = h.volume_stats(reqs, w)
+        wall = (time.perf_counter() - t0) / reps
+        kt = h.get_timing()
+        h.set_timing(False)
+        other_ms = kt["other"][0] / reps
+        # each pass reads the mask of every streamed row and the FP64 pair of the structure rows
+        by = n_pass * (plan.n_vox * 4 + n_struct * 16)
+        out[name] = {"requests": len(reqs), "ms_per_call": wall * 1e3, "final_pass_ms": kt["forward"][0] / reps,
+                     "stats_kernels_ms": other_ms, "stats_launches": 1 if n_pass == 1 else 9,
+                     "stats_bytes": by, "stats_achieved_gbs": by / (other_ms * 1e-3) / 1e9 if other_ms else None,
+                     "peak": hbm}
+        if name == "values_at_volume":
+            out[name]["results"] = {f"{r['quantity']}:{r['struct_bit']}": [float(x) for x in v["at_volume"]]
+                                    for r, v in zip(reqs, res)}
+    h.close()
+    out["note"] = ("%d structure voxels of %d rows; the statistics kernels read 4 B of mask per row and 16 B of "
+                   "FP64 (Dw, Lw) per structure voxel per pass, mostly from L2 right after the final pass: "
+                   "launch- and L2-bound, not an HBM roofline" % (n_struct, plan.n_vox))
+    return out
+
+
 def cpu_baseline(plan, iters):
     """FP64 oracle, as it stands, on `iters` iterations of the same plan."""
     import oracle
@@ -596,6 +649,8 @@ def main():
                     help="skip the batching workloads in the default run")
     ap.add_argument("--no-robust", dest="robust", action="store_false")
     ap.add_argument("--batch-iters", type=int, default=100)
+    ap.add_argument("--no-volume", dest="volume", action="store_false",
+                    help="skip the volume-statistics timing (DVH, values at volume)")
     args = ap.parse_args()
     if args.batching:
         import torch

@@ -77,9 +77,11 @@ typedef struct fredopt_constraint {
   double priority;     /* structure weight p_S > 0 (Fig. 2 "w_i"; Sec. 2.4.3) */
 } fredopt_constraint;
 
-/* objective quantities of Eq. 2: q_i = (D w)_i or c (L w)_i */
+/* objective quantities of Eq. 2: q_i = (D w)_i or c (L w)_i; the volume
+ * statistics also take LETd_i = (L w)_i / (D w)_i (Eq. 1, 0 where (D w)_i = 0) */
 #define FREDOPT_Q_DOSE 0
 #define FREDOPT_Q_CDL 1
+#define FREDOPT_Q_LETD 2
 
 typedef struct fredopt_objective_term {
   uint32_t struct_bit; /* structure whose voxels enter this term */
@@ -224,6 +226,58 @@ int fredopt_feasibility_step(fredopt_t h, const float* x, double relaxation, dou
 
 /* Objective f(x) (Eq. 2 terms, FP64 reduction) and its gradient g (float[n_spots]). */
 int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_out, uint32_t flags);
+
+/* ---- volume statistics of a plan (Sec. 2.4.1: DVH, LVH, cDLVH; cDL30; the
+ * PTV rule "98% of the volume receives at least 95% of the prescription") ----
+ *
+ * The voxel values are those of fredopt_end's final pass: (D w)_i and
+ * (L w)_i accumulated in FP64 over the stored values, then rounded once to
+ * FP32 as dose = (D w)_i, LETd = (L w)_i / (D w)_i (0 where (D w)_i <= 0),
+ * cDL = c_cdl (L w)_i, with c_cdl of the last begin (default 0.04 um/keV).
+ * A structure is the set of voxels whose mask has bit struct_bit set.
+ *
+ * Per request:
+ *   counts[b]    = number of the structure's voxels with
+ *                  edges[b] <= v < edges[b+1], b < n_bins (half-open bins;
+ *                  a last edge of +INFINITY makes the last bin cumulative);
+ *                  edges: n_bins + 1 non-decreasing, non-NaN floats.
+ *   at_volume[q] = the value received by the fraction fracs[q] of the
+ *                  structure's volume: its k-th largest value with
+ *                  k = ceil(fracs[q] * n), n = n_voxels; the product is taken
+ *                  in FP64 and a product within 1e-9 * max(1, product) of an
+ *                  integer counts as that integer; k is kept in [1, n]; NaN
+ *                  when n = 0.  fracs in (0, 1].  The result is one of the
+ *                  voxel values, bit for bit (an exact radix selection).
+ *   n_voxels     = voxels in the structure.
+ * All request arrays are host memory owned by the caller. */
+typedef struct fredopt_volume_request {
+  int32_t quantity;   /* FREDOPT_Q_DOSE, FREDOPT_Q_CDL or FREDOPT_Q_LETD */
+  int32_t struct_bit; /* 0..31 */
+  int32_t n_bins;     /* 0..FREDOPT_VOLUME_MAX_BINS in total over the requests */
+  int32_t n_fracs;    /* 0..FREDOPT_VOLUME_MAX_FRACS in total over the requests */
+  const float* edges; /* [n_bins + 1] (NULL when n_bins = 0) */
+  const double* fracs;/* [n_fracs] (NULL when n_fracs = 0) */
+  int64_t* counts;    /* out [n_bins] */
+  float* at_volume;   /* out [n_fracs] */
+  int64_t n_voxels;   /* out */
+} fredopt_volume_request; /* 56 bytes */
+
+#define FREDOPT_VOLUME_MAX_REQUESTS 64
+#define FREDOPT_VOLUME_MAX_BINS 16384
+#define FREDOPT_VOLUME_MAX_FRACS 64
+
+/* Volume statistics of fluence w (float[n_spots]; host, or device with
+ * FREDOPT_DEVICE_PTR in flags; NULL = the current iterate of a begun solve)
+ * for n_req requests, from one final pass.  Needs a loaded plan.  Errors:
+ * FREDOPT_ERR_INVALID_ARG for a bad request (kind, bit, sizes, unsorted or
+ * NaN edges, fractions outside (0, 1]); the handle stays usable.  Does not
+ * change the solve state. */
+int fredopt_volume_stats(fredopt_t h, const float* w, uint32_t flags, int n_req, fredopt_volume_request* req);
+
+/* The per-voxel map (float[n_vox], voxel order; host, or device with
+ * FREDOPT_DEVICE_PTR) of one quantity for fluence w (as above), with the
+ * values fredopt_volume_stats uses. */
+int fredopt_quantity_map(fredopt_t h, const float* w, int quantity, float* out, uint32_t flags);
 
 /* ---- inspection of the device data (bit-exact copies) ---- */
 

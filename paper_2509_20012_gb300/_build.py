@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfredopt.so")
-SOURCES = ["fredopt_kernels.cu", "fredopt_api.cu", "fredopt_server.cu", "fredopt_noalloc.cu"]
+SOURCES = ["fredopt_kernels.cu", "fredopt_api.cu", "fredopt_server.cu", "fredopt_noalloc.cu", "fredopt_volume.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

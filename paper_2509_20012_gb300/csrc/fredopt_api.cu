@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -102,6 +103,7 @@ struct fredopt_ctx {
   DBuf<float2> yw, yg, r, gam, yall;
   DBuf<double2> y64;
   DBuf<float> chunk_sum, fout_a, fout_b, vin_a, vin_b;
+  DBuf<uint8_t> vol_buf;  // volume statistics scratch
   DBuf<double> part;
   DBuf<DevState> st;
   DBuf<LogEntry> log;
@@ -501,6 +503,51 @@ int check_sticky(fredopt_t h) {
   return FREDOPT_OK;
 }
 
+// FP64 pass of every row for w (host or device per flags; null = the current
+// iterate of a begun solve) into y64, as in fredopt_end.
+int final_pass_y64(fredopt_t h, const float* w, uint32_t flags) {
+  cudaStream_t s = h->stream;
+  const float* x = nullptr;
+  if (w) {
+    int rc = load_spot_vec(h, h->xbuf, w, flags);
+    if (rc) return rc;
+    x = h->xbuf.p;
+  } else {
+    if (!h->begun) return fail(h, FREDOPT_ERR_NOT_LOADED, "w is null and no solve is begun");
+    x = h->w.p;
+  }
+  CK(h->y64.ensure(std::max<int64_t>(1, h->V)));
+  CK(cudaMemsetAsync(h->y64.p, 0, std::max<int64_t>(1, h->V) * sizeof(double2), s));
+  FwdArgs fa = fwd_args(h, false);
+  fa.x = x;
+  fa.y64 = h->y64.p;
+  fa.dose_out = nullptr;
+  fa.letd_out = nullptr;
+  run(h, 0, [&] { launch_forward(h->geo, h->fmt, EPI_FINAL, false, fa, h->tab, s); });
+  CK(cudaGetLastError());
+  return FREDOPT_OK;
+}
+
+// Rank k (1 = largest) of the value received by the fraction `frac` of n
+// voxels: ceil(frac * n), a product within 1e-9 * max(1, product) of an
+// integer counting as that integer, kept in [1, n].
+int64_t at_volume_rank(double frac, int64_t n) {
+  volatile double t = frac * (double)n;  // rounded product (never fused with what follows)
+  const double tv = t;
+  const double r = std::floor(tv + 0.5);
+  const double k = (std::fabs(tv - r) <= 1e-9 * std::max(1.0, tv)) ? r : std::ceil(tv);
+  return std::min<int64_t>(std::max<int64_t>((int64_t)k, 1), n);
+}
+
+float key_to_float(uint32_t key) {
+  const uint32_t u = (key & 0x80000000u) ? (key & 0x7fffffffu) : ~key;
+  float f;
+  std::memcpy(&f, &u, sizeof(f));
+  return f;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 }  // namespace
 
 // =================================================================== ABI
@@ -745,20 +792,24 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   for (int64_t r = 0; r < n_hot; ++r) h->h_mask[r] = m0[order[r]];
   CK(upload_vec(h, h->mask, h->h_mask));
   CK(h->mdd.alloc(n_hot)); CK(h->mll.alloc(n_hot)); CK(h->mdl.alloc(n_hot));
-  launch_moments(fmt, h->rp.p, n_hot, h->Dv.p, h->Lv.p, fmt ? h->sD.p : nullptr, fmt ? h->sL.p : nullptr,
+  CK(cudaMemsetAsync(h->mdd.p, 0, std::max<int64_t>(1, n_hot) * sizeof(double), s));
+  CK(cudaMemsetAsync(h->mll.p, 0, std::max<int64_t>(1, n_hot) * sizeof(double), s));
+  CK(cudaMemsetAsync(h->mdl.p, 0, std::max<int64_t>(1, n_hot) * sizeof(double), s));
+  launch_moments(fmt, h->rp.p, n_hot_ne, h->Dv.p, h->Lv.p, fmt ? h->sD.p : nullptr, fmt ? h->sL.p : nullptr,
                  h->mdd.p, h->mll.p, h->mdl.p, s);
   CK(cudaGetLastError());
 
   // ---- CSC copy of the streamed rows (blocked stable counting transpose)
   {
-    const int n_blk = (int)std::max<int64_t>(1, std::min<int64_t>(2 * h->geo.n_sms, n_hot));
-    std::vector<int64_t> blk = partition_rows(rpd, n_hot, n_blk, 1);
+    // rows without nonzeros (after the others in device order) add nothing
+    const int n_blk = (int)std::max<int64_t>(1, std::min<int64_t>(2 * h->geo.n_sms, n_hot_ne));
+    std::vector<int64_t> blk = partition_rows(rpd, n_hot_ne, n_blk, 1);
     DBuf<int64_t> blk_d, tot_d;
     DBuf<int32_t> cnt;
     CK(upload_vec(h, blk_d, blk));
     CK(cnt.alloc((size_t)n_blk * n_spots));
     CK(cudaMemsetAsync(cnt.p, 0, (size_t)n_blk * n_spots * sizeof(int32_t), s));
-    if (n_hot > 0) launch_csc_count(h->rp.p, h->col.p, blk_d.p, n_blk, n_spots, cnt.p, s);
+    if (n_hot_ne > 0) launch_csc_count(h->rp.p, h->col.p, blk_d.p, n_blk, n_spots, cnt.p, s);
     CK(tot_d.alloc(n_spots));
     launch_csc_colsum(cnt.p, n_blk, n_spots, tot_d.p, s);
     CK(cudaGetLastError());
@@ -778,7 +829,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(cudaMemsetAsync(h->crow.p + h->nnz_hot, 0, (nh_alloc - h->nnz_hot) * sizeof(int32_t), s));
     CK(cudaMemsetAsync(h->DTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
     CK(cudaMemsetAsync(h->LTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
-    if (n_hot > 0)
+    if (n_hot_ne > 0)
       launch_csc_fill(fmt, h->rp.p, h->col.p, h->Dv.p, h->Lv.p, blk_d.p, n_blk, n_spots, cnt.p,
                       h->crow.p, h->DTv.p, h->LTv.p, s);
     CK(cudaGetLastError());
@@ -1321,6 +1372,153 @@ int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_ou
     *f_out = f;
   }
   return FREDOPT_OK;
+}
+
+int fredopt_volume_stats(fredopt_t h, const float* w, uint32_t flags, int n_req, fredopt_volume_request* req) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (n_req < 0 || n_req > FREDOPT_VOLUME_MAX_REQUESTS || (n_req > 0 && !req))
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "need 0 <= n_req <= FREDOPT_VOLUME_MAX_REQUESTS and req");
+  VolArgs va{};
+  SelArgs sa{};
+  std::vector<float> edges;
+  std::vector<double> fracs;
+  std::vector<int> sel_req;
+  int n_bins = 0;
+  for (int i = 0; i < n_req; ++i) {
+    const fredopt_volume_request& r = req[i];
+    if (r.quantity < FREDOPT_Q_DOSE || r.quantity > FREDOPT_Q_LETD)
+      return fail(h, FREDOPT_ERR_INVALID_ARG, "quantity must be FREDOPT_Q_DOSE, _CDL or _LETD");
+    if (r.struct_bit < 0 || r.struct_bit > 31) return fail(h, FREDOPT_ERR_INVALID_ARG, "struct_bit must be 0..31");
+    if (r.n_bins < 0 || r.n_fracs < 0) return fail(h, FREDOPT_ERR_INVALID_ARG, "negative n_bins or n_fracs");
+    if (r.n_bins > 0 && (!r.edges || !r.counts)) return fail(h, FREDOPT_ERR_INVALID_ARG, "edges or counts is null");
+    if (r.n_fracs > 0 && (!r.fracs || !r.at_volume))
+      return fail(h, FREDOPT_ERR_INVALID_ARG, "fracs or at_volume is null");
+    if (n_bins + (int64_t)r.n_bins > FREDOPT_VOLUME_MAX_BINS)
+      return fail(h, FREDOPT_ERR_INVALID_ARG, "more than FREDOPT_VOLUME_MAX_BINS bins in total");
+    if ((int64_t)fracs.size() + r.n_fracs > FREDOPT_VOLUME_MAX_FRACS)
+      return fail(h, FREDOPT_ERR_INVALID_ARG, "more than FREDOPT_VOLUME_MAX_FRACS fractions in total");
+    for (int b = 0; b <= r.n_bins && r.n_bins > 0; ++b) {
+      if (std::isnan(r.edges[b])) return fail(h, FREDOPT_ERR_INVALID_ARG, "NaN edge");
+      if (b > 0 && r.edges[b] < r.edges[b - 1]) return fail(h, FREDOPT_ERR_INVALID_ARG, "edges decrease");
+    }
+    for (int q = 0; q < r.n_fracs; ++q)
+      if (!(r.fracs[q] > 0.0 && r.fracs[q] <= 1.0)) return fail(h, FREDOPT_ERR_INVALID_ARG, "fraction outside (0, 1]");
+    va.q[i] = r.quantity;
+    va.bit[i] = r.struct_bit;
+    va.nb[i] = r.n_bins;
+    va.eoff[i] = (int32_t)edges.size();
+    va.boff[i] = n_bins;
+    if (r.n_bins > 0) edges.insert(edges.end(), r.edges, r.edges + r.n_bins + 1);
+    n_bins += r.n_bins;
+    for (int q = 0; q < r.n_fracs; ++q) {
+      const int j = (int)fracs.size();
+      sa.q[j] = r.quantity;
+      sa.bit[j] = r.struct_bit;
+      sel_req.push_back(i);
+      fracs.push_back(r.fracs[q]);
+    }
+    va.any_bits |= 1u << r.struct_bit;
+  }
+  if (n_req == 0) return FREDOPT_OK;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  join_in(h);
+  rc = final_pass_y64(h, w, flags);
+  if (rc) return rc;
+
+  // scratch: edges | counts | n_vox | digit histograms | selection slots
+  const int n_sel = (int)fracs.size();
+  const size_t o_edges = 0;
+  const size_t o_counts = o_edges + align256(std::max<size_t>(1, edges.size()) * sizeof(float));
+  const size_t o_nvox = o_counts + align256(std::max(1, n_bins) * sizeof(unsigned long long));
+  const size_t o_hist = o_nvox + align256(n_req * sizeof(unsigned long long));
+  const size_t o_slot = o_hist + align256(std::max(1, n_sel) * 256 * sizeof(uint32_t));
+  const size_t total = o_slot + align256(std::max(1, n_sel) * sizeof(SelSlot));
+  CK(h->vol_buf.ensure(total));
+  uint8_t* base = h->vol_buf.p;
+  CK(cudaMemsetAsync(base + o_counts, 0, o_slot - o_counts, s));
+  if (!edges.empty())
+    CK(cudaMemcpyAsync(base + o_edges, edges.data(), edges.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+
+  va.y64 = h->y64.p;
+  va.mask = h->mask.p;
+  va.n_rows = h->n_hot;  // every structure voxel is a streamed row
+  va.c = h->tab.c;
+  va.n_req = n_req;
+  va.n_edges = (int)edges.size();
+  va.n_bins = n_bins;
+  va.edges = reinterpret_cast<const float*>(base + o_edges);
+  va.counts = reinterpret_cast<unsigned long long*>(base + o_counts);
+  va.n_vox = reinterpret_cast<unsigned long long*>(base + o_nvox);
+  run(h, 5, [&] { launch_vol_hist(h->geo, va, s); });
+  CK(cudaGetLastError());
+  std::vector<unsigned long long> nvox(n_req);
+  CK(cudaMemcpyAsync(nvox.data(), va.n_vox, n_req * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+
+  std::vector<SelSlot> slots(std::max(1, n_sel));
+  if (n_sel > 0) {
+    for (int j = 0; j < n_sel; ++j) {
+      const int64_t n = (int64_t)nvox[sel_req[j]];
+      slots[j].prefix = 0u;
+      slots[j].pad = 0u;
+      slots[j].k = n > 0 ? (uint64_t)at_volume_rank(fracs[j], n) : 0u;
+    }
+    sa.y64 = h->y64.p;
+    sa.mask = h->mask.p;
+    sa.n_rows = h->n_hot;
+    sa.c = h->tab.c;
+    sa.any_bits = va.any_bits;
+    sa.n_sel = n_sel;
+    sa.hist = reinterpret_cast<uint32_t*>(base + o_hist);
+    sa.st = reinterpret_cast<SelSlot*>(base + o_slot);
+    CK(cudaMemcpyAsync(sa.st, slots.data(), n_sel * sizeof(SelSlot), cudaMemcpyHostToDevice, s));
+    run(h, 5, [&] { launch_vol_select(h->geo, sa, s); });
+    h->launches += 7;  // launch_vol_select enqueues 8 kernels
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(slots.data(), sa.st, n_sel * sizeof(SelSlot), cudaMemcpyDeviceToHost, s));
+  }
+  std::vector<unsigned long long> counts(std::max(1, n_bins));
+  if (n_bins > 0)
+    CK(cudaMemcpyAsync(counts.data(), va.counts, n_bins * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  rc = check_sticky(h);
+  collect_timers(h);
+  if (rc) return rc;
+  int j = 0;
+  for (int i = 0; i < n_req; ++i) {
+    fredopt_volume_request& r = req[i];
+    r.n_voxels = (int64_t)nvox[i];
+    for (int b = 0; b < r.n_bins; ++b) r.counts[b] = (int64_t)counts[va.boff[i] + b];
+    for (int q = 0; q < r.n_fracs; ++q, ++j)
+      r.at_volume[q] = nvox[i] > 0 ? key_to_float(slots[j].prefix) : std::numeric_limits<float>::quiet_NaN();
+  }
+  return FREDOPT_OK;
+}
+
+int fredopt_quantity_map(fredopt_t h, const float* w, int quantity, float* out, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!out) return fail(h, FREDOPT_ERR_INVALID_ARG, "out is null");
+  if (quantity < FREDOPT_Q_DOSE || quantity > FREDOPT_Q_LETD)
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "quantity must be FREDOPT_Q_DOSE, _CDL or _LETD");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = h->stream;
+  join_in(h);
+  rc = final_pass_y64(h, w, flags);
+  if (rc) return rc;
+  float* dst = out;
+  if (!dev_ptr(flags)) {
+    CK(h->fout_a.ensure(std::max<int64_t>(1, h->V)));
+    dst = h->fout_a.p;
+  }
+  run(h, 5, [&] { launch_vol_map(h->geo, h->y64.p, h->perm ? h->voxel.p : nullptr, h->V, quantity, h->tab.c, dst, s); });
+  CK(cudaGetLastError());
+  if (!dev_ptr(flags) && h->V > 0)
+    CK(cudaMemcpyAsync(out, dst, h->V * sizeof(float), cudaMemcpyDeviceToHost, s));
+  rc = check_sticky(h);
+  collect_timers(h);
+  return rc;
 }
 
 int fredopt_get_sizes(fredopt_t h, int64_t* n_vox, int64_t* n_spots, int64_t* nnz, int64_t* n_rows,

@@ -217,6 +217,49 @@ void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_
 void launch_scale_coef(int64_t n, const float* aD, const float* aL, const int64_t* voxel,
                        const float* sD, const float* sL, float2* coef, cudaStream_t s);
 
+// ---- volume statistics (fredopt_volume.cu)
+constexpr int kMaxVolReq = 64;  // requests per call
+constexpr int kMaxSel = 64;     // (request, fraction) selections per call
+
+// histograms: request i bins its structure's values with the packed edges
+// [eoff[i], eoff[i] + nb[i]] into the packed counts [boff[i], boff[i] + nb[i])
+struct VolArgs {
+  const double2* y64;       // FP64 (Dw, Lw) per device row
+  const uint32_t* mask;     // per device row
+  int64_t n_rows;
+  double c;                 // cDL constant
+  uint32_t any_bits;        // union of the requested structure bits
+  int n_req, n_edges, n_bins;
+  int32_t q[kMaxVolReq], bit[kMaxVolReq], nb[kMaxVolReq], eoff[kMaxVolReq], boff[kMaxVolReq];
+  const float* edges;
+  unsigned long long* counts;  // [n_bins], zeroed by the caller
+  unsigned long long* n_vox;   // [n_req], zeroed by the caller
+};
+
+struct SelSlot {
+  uint32_t prefix;  // key bits chosen so far (the answer's key after the last pass)
+  uint32_t pad;
+  uint64_t k;       // rank (1 = largest) among the values matching the prefix; 0 = empty
+};
+
+struct SelArgs {
+  const double2* y64;
+  const uint32_t* mask;
+  int64_t n_rows;
+  double c;
+  uint32_t any_bits;
+  int n_sel;
+  int32_t q[kMaxSel], bit[kMaxSel];
+  uint32_t* hist;  // [n_sel][256], zeroed by the caller
+  SelSlot* st;     // [n_sel]
+};
+
+size_t vol_hist_smem(const VolArgs& a);
+void launch_vol_hist(const Geometry& g, const VolArgs& a, cudaStream_t s);
+void launch_vol_select(const Geometry& g, const SelArgs& a, cudaStream_t s);  // 8 launches
+void launch_vol_map(const Geometry& g, const double2* y64, const int64_t* voxel, int64_t n_rows, int q, double c,
+                    float* out, cudaStream_t s);
+
 // handle internals used by the serving loop (fredopt_server.cu)
 cudaStream_t handle_stream(::fredopt_ctx* h);
 int handle_device(::fredopt_ctx* h);

@@ -928,12 +928,18 @@ __global__ void k_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int
 // Rows of a block in ascending order; within a row all columns differ, so
 // the cursor updates of one row never collide; a barrier separates rows,
 // which keeps the rows of every column ascending (a stable transpose).
-template <typename VT>
+template <typename VT, bool SMEM>
 __global__ void k_csc_fill(const int64_t* rp, const int32_t* col, const VT* Dv, const VT* Lv,
                            const int64_t* blk_row, int32_t n_cols, int32_t* cursor, int32_t* row_out,
                            VT* DT, VT* LT) {
+  extern __shared__ int32_t sh_cur[];
   const int b = blockIdx.x;
   int32_t* cur = cursor + (int64_t)b * n_cols;
+  if (SMEM) {  // the block's cursors stay in shared memory for the whole pass
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) sh_cur[j] = cur[j];
+    __syncthreads();
+    cur = sh_cur;
+  }
   for (int64_t r = blk_row[b]; r < blk_row[b + 1]; ++r) {
     const int64_t s = rp[r], e = rp[r + 1];
     for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) {
@@ -1190,16 +1196,35 @@ void launch_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int64_t* 
   k_csc_offsets<<<(n_cols + 255) / 256, 256, 0, s>>>(cnt, n_blk, n_cols, cp);
 }
 
+constexpr size_t kCscFillSmemMax = 200 * 1024;
+
 void launch_csc_fill(int fmt, const int64_t* rp, const int32_t* col, const void* Dv, const void* Lv,
                      const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor,
                      int32_t* row_out, void* DT, void* LT, cudaStream_t s) {
-  if (fmt == 0)
-    k_csc_fill<float><<<n_blk, 256, 0, s>>>(rp, col, (const float*)Dv, (const float*)Lv, blk_row,
-                                            n_cols, cursor, row_out, (float*)DT, (float*)LT);
-  else
-    k_csc_fill<uint16_t><<<n_blk, 256, 0, s>>>(rp, col, (const uint16_t*)Dv, (const uint16_t*)Lv,
-                                               blk_row, n_cols, cursor, row_out, (uint16_t*)DT,
-                                               (uint16_t*)LT);
+  // cursors in shared memory when one block's row of the table fits
+  const size_t smem = (size_t)n_cols * sizeof(int32_t);
+  const bool use_smem = smem <= kCscFillSmemMax;
+  if (fmt == 0) {
+    if (use_smem) {
+      cudaFuncSetAttribute(k_csc_fill<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_csc_fill<float, true><<<n_blk, 256, smem, s>>>(rp, col, (const float*)Dv, (const float*)Lv, blk_row,
+                                                       n_cols, cursor, row_out, (float*)DT, (float*)LT);
+    } else {
+      k_csc_fill<float, false><<<n_blk, 256, 0, s>>>(rp, col, (const float*)Dv, (const float*)Lv, blk_row,
+                                                     n_cols, cursor, row_out, (float*)DT, (float*)LT);
+    }
+  } else {
+    if (use_smem) {
+      cudaFuncSetAttribute(k_csc_fill<uint16_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_csc_fill<uint16_t, true><<<n_blk, 256, smem, s>>>(rp, col, (const uint16_t*)Dv, (const uint16_t*)Lv,
+                                                          blk_row, n_cols, cursor, row_out, (uint16_t*)DT,
+                                                          (uint16_t*)LT);
+    } else {
+      k_csc_fill<uint16_t, false><<<n_blk, 256, 0, s>>>(rp, col, (const uint16_t*)Dv, (const uint16_t*)Lv,
+                                                        blk_row, n_cols, cursor, row_out, (uint16_t*)DT,
+                                                        (uint16_t*)LT);
+    }
+  }
 }
 
 void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_t* row, const void* DT,

@@ -22,7 +22,8 @@ DEVICE_PTR = 0x1
 FORMATS = {"fp32": 0, "bf16": 1, "fp16": 2}
 ROWS = {"all": 0x000, "roi": 0x100}
 KINDS = {"DOSE_MIN": 0, "DOSE_MAX": 1, "CDL_MIN": 2, "CDL_MAX": 3, "LETD_MIN": 4, "LETD_MAX": 5}
-QUANTITIES = {"DOSE": 0, "CDL": 1}
+QUANTITIES = {"DOSE": 0, "CDL": 1, "LETD": 2}  # LETD: volume statistics only
+VOLUME_MAX_REQUESTS, VOLUME_MAX_BINS, VOLUME_MAX_FRACS = 64, 16384, 64
 NORMS = {"all": 0, "violated": 1}
 KCLASS_N = 6
 KCLASS_NAMES = ["forward", "backward", "constraints", "colfinish", "finish", "other"]
@@ -94,6 +95,12 @@ class TicketInfo(ctypes.Structure):
         return d
 
 
+class VolumeRequest(ctypes.Structure):
+    _fields_ = [("quantity", ctypes.c_int32), ("struct_bit", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("n_fracs", ctypes.c_int32), ("edges", ctypes.c_void_p), ("fracs", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p), ("at_volume", ctypes.c_void_p), ("n_voxels", ctypes.c_int64)]
+
+
 QUEUED, LOADING, RUNNING, DONE = 0, 1, 2, 3
 
 _lib = None
@@ -131,6 +138,10 @@ _SIGS = {
                                                 ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32]),
     "fredopt_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_void_p, ctypes.c_uint32]),
+    "fredopt_volume_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int,
+                                            ctypes.POINTER(VolumeRequest)]),
+    "fredopt_quantity_map": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_uint32]),
     "fredopt_get_sizes": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 5),
     "fredopt_get_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fredopt_get_csc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -400,6 +411,58 @@ class Handle:
         self._check(self.lib.fredopt_objective(self.h, _ptr(x, np.float32)[0], ctypes.byref(f),
                                                _ptr(g, np.float32)[0], DEVICE_PTR if dev else 0))
         return f.value, g
+
+    # ---------------------------------------------------------- volume statistics
+    def volume_stats(self, requests, w=None):
+        """fredopt_volume_stats.  requests: dicts with quantity ("DOSE", "CDL",
+        "LETD"), struct_bit, and optional edges (n_bins + 1 floats) and fracs.
+        w: fluence (host or CUDA), None = the current iterate of a begun solve.
+        Returns one dict per request: counts (int64[n_bins]), at_volume
+        (float32[n_fracs]), n_voxels."""
+        arr = (VolumeRequest * max(1, len(requests)))()
+        keep, outs = [], []
+        for i, r in enumerate(requests):
+            edges = None if r.get("edges") is None else np.ascontiguousarray(r["edges"], np.float32)
+            fracs = None if r.get("fracs") is None else np.ascontiguousarray(r["fracs"], np.float64)
+            nb = 0 if edges is None else max(0, len(edges) - 1)
+            nf = 0 if fracs is None else len(fracs)
+            counts = np.zeros(max(1, nb), np.int64)
+            at = np.zeros(max(1, nf), np.float32)
+            keep += [edges, fracs]
+            outs.append((counts, at, nb, nf))
+            arr[i] = VolumeRequest(QUANTITIES[r["quantity"]], int(r["struct_bit"]), nb, nf,
+                                   edges.ctypes.data if nb else None, fracs.ctypes.data if nf else None,
+                                   counts.ctypes.data, at.ctypes.data, 0)
+        dev = w is not None and _on_device(w)
+        p, kw = _ptr(w, np.float32)
+        self._check(self.lib.fredopt_volume_stats(self.h, p, DEVICE_PTR if dev else 0, len(requests), arr))
+        return [{"counts": c[:nb], "at_volume": a[:nf], "n_voxels": int(arr[i].n_voxels)}
+                for i, (c, a, nb, nf) in enumerate(outs)]
+
+    def quantity_map(self, w, quantity):
+        """fredopt_quantity_map: the per-voxel DOSE, CDL or LETD map (voxel order)
+        of fluence w (None = the current iterate of a begun solve)."""
+        dev = w is not None and _on_device(w)
+        out = self._out(dev, self.n_vox)
+        self._check(self.lib.fredopt_quantity_map(self.h, _ptr(w, np.float32)[0], QUANTITIES[quantity],
+                                                  _ptr(out, np.float32)[0], DEVICE_PTR if dev else 0))
+        return out
+
+    def derive_cdl_limits(self, w, oar_bits, frac=0.30, priority=1.0):
+        """CDL_MAX constraints at the cDL value received by `frac` of each OAR's
+        volume for fluence w (cDL30 for frac = 0.3)."""
+        res = self.volume_stats([{"quantity": "CDL", "struct_bit": b, "fracs": [frac]} for b in oar_bits], w)
+        return [{"struct_bit": int(b), "kind": "CDL_MAX", "bound": float(r["at_volume"][0]),
+                 "priority": float(priority)} for b, r in zip(oar_bits, res)]
+
+    def coverage(self, ptv_bit, prescription, w=None, volume=0.98, level=0.95):
+        """PTV coverage rule: (value received by `volume` of the PTV, voxels at
+        or above level * prescription, PTV voxels, rule satisfied)."""
+        t = np.float32(level * prescription)
+        r = self.volume_stats([{"quantity": "DOSE", "struct_bit": ptv_bit, "fracs": [volume],
+                                "edges": [t, np.inf]}], w)[0]
+        d = float(r["at_volume"][0])
+        return d, int(r["counts"][0]), r["n_voxels"], bool(d >= t)
 
     # ---------------------------------------------------------- inspection
     def get_rows(self):

@@ -78,10 +78,12 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "fredopt.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fredopt_params), sizeof(fredopt_report),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fredopt_params), sizeof(fredopt_report),
          sizeof(fredopt_request), sizeof(fredopt_ticket_info), sizeof(fredopt_log_entry),
          sizeof(fredopt_constraint), sizeof(fredopt_objective_term), offsetof(fredopt_request, params),
-         offsetof(fredopt_request, w_out), offsetof(fredopt_request, alpha), offsetof(fredopt_ticket_info, report));
+         offsetof(fredopt_request, w_out), offsetof(fredopt_request, alpha), offsetof(fredopt_ticket_info, report),
+         sizeof(fredopt_volume_request), offsetof(fredopt_volume_request, edges),
+         offsetof(fredopt_volume_request, n_voxels));
   return 0;
 }
 ''')
@@ -90,5 +92,6 @@ int main(void) {
     c = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     py = [ctypes.sizeof(f.Params), ctypes.sizeof(f.Report), ctypes.sizeof(f.Request), ctypes.sizeof(f.TicketInfo),
           ctypes.sizeof(f.LogEntry), ctypes.sizeof(f.Constraint), ctypes.sizeof(f.ObjectiveTerm),
-          f.Request.params.offset, f.Request.w_out.offset, f.Request.alpha.offset, f.TicketInfo.report.offset]
+          f.Request.params.offset, f.Request.w_out.offset, f.Request.alpha.offset, f.TicketInfo.report.offset,
+          ctypes.sizeof(f.VolumeRequest), f.VolumeRequest.edges.offset, f.VolumeRequest.n_voxels.offset]
     assert c == py
