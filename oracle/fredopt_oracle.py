@@ -49,6 +49,16 @@ inconsistent):
       constraint); rows are ordered by constraint table order, then voxel.
   R12 LETd output = Lw/Dw where Dw > 0, else 0 (Eq. 1 with the denominator
       taken as the dose, Sec. 2.2).
+  R13 Block-iterative form of Fig. 2 (`block_iterative_sweep`): the rows are
+      split into blocks that are visited in turn; inside a block the rows are
+      projected simultaneously at the block's starting point with weights
+      p_r / W_B (W_B over the block's reachable rows, or its violated rows),
+      so a single block is R1's Cimmino step and one row per block is Fig. 2's
+      row-action sweep with unit priorities.  Fluence >= 0 is imposed once,
+      after the sweep, as in Fig. 2's last loop.  The blocks used for plans
+      (`sweep_blocks`) are groups of S = ceil(|C| / n_blocks) consecutive
+      voxels of C, the voxels that lie in a structure and have influence
+      entries, in ascending voxel order; all rows of a voxel share its block.
 """
 from __future__ import annotations
 
@@ -231,6 +241,44 @@ def sequential_ams_sweep(R: Rows, x, lam: float, prio_scale: float = 1.0, clip: 
     return x
 
 
+def sweep_blocks(P: Problem, R: Rows, n_blocks: int):
+    """Blocks of R13: row indices of R per block, in visiting order."""
+    nz = np.diff(P.D.indptr) > 0
+    C = np.nonzero((P.mask != 0) & nz)[0]
+    if len(C) == 0:
+        return []
+    S = -(-len(C) // max(1, int(n_blocks)))
+    group = np.full(P.n_vox, -1, np.int64)
+    group[C] = np.arange(len(C)) // S
+    g = group[R.voxel]
+    return [np.nonzero(g == b)[0] for b in range(int(group[C[-1]]) + 1)]
+
+
+def block_iterative_sweep(R: Rows, x, lam: float, blocks, prio_scale: float = 1.0, norm: str = "all",
+                          clip: bool = True):
+    """One block-iterative sweep (R13): for each block B in order, from the
+    current point x, x <- x + lam * prio_scale * sum_{r in B} (p_r / W_B) t_r a_r
+    with t_r = (b_r - a_r.x)/|a_r|^2 for the violated rows of B (R3); then
+    fluence >= 0."""
+    x = np.array(x, np.float64)
+    for B in blocks:
+        A = R.A[B]
+        v = A @ x
+        viol = np.where(R.upper[B], v > R.b[B], v < R.b[B])
+        t = np.where(viol, (R.b[B] - v) / R.norm2[B], 0.0)
+        if norm == "all":
+            W = R.p[B].sum()
+        elif norm == "violated":
+            W = R.p[B][viol].sum()
+        else:
+            raise ValueError(norm)
+        if W > 0:
+            x = x + lam * (A.T @ (prio_scale * R.p[B] / W * t))
+    if clip:
+        x = np.maximum(x, 0.0)
+    return x
+
+
 # ---------------------------------------------------------------- objective
 
 def _term_rows(P: Problem, term):
@@ -268,14 +316,15 @@ def objective_gradient(P: Problem, x):
 def superiorize(P: Problem, w0, iters: int, alpha: float, lam: float, beta0: float | None = None,
                 eta: float = 1.0, reductions: int = 1, max_trials: int = 50, norm: str = "all",
                 grad_normalize: bool = True, sequential: bool = False, rows: Rows | None = None,
-                s0: int = 0, k0: int = 0):
+                s0: int = 0, k0: int = 0, sweep: int = 0):
     """Superiorized feasibility seeking (Fig. 3 with R4-R8).
 
     For k = 0..iters-1: perturbation phase from w^k (reductions steps, each a
     trial loop with beta = beta0*alpha^s, s advancing on every trial, accepted
     when f does not ascend, f evaluated afresh at every trial), then one
-    feasibility step (Cimmino, or the Fig. 2 sweep if sequential=True) from the
-    perturbed point with priorities scaled by eta^k.
+    feasibility step (Cimmino; the block-iterative sweep of R13 over `sweep`
+    blocks if sweep > 0; the Fig. 2 row-action sweep if sequential=True) from
+    the perturbed point with priorities scaled by eta^k.
 
     Returns (w, log); log[k] = dict(k, s, accepted, beta, f_start, f_end, gnorm).
     """
@@ -283,6 +332,7 @@ def superiorize(P: Problem, w0, iters: int, alpha: float, lam: float, beta0: flo
     if beta0 is None:
         beta0 = 0.1 * float(np.linalg.norm(w))
     R = constraint_rows(P) if rows is None else rows
+    blocks = sweep_blocks(P, R, sweep) if sweep > 0 else None
     s = int(s0)
     log = []
     for k in range(k0, k0 + iters):
@@ -309,6 +359,8 @@ def superiorize(P: Problem, w0, iters: int, alpha: float, lam: float, beta0: flo
         scale = eta ** k
         if sequential:
             w = sequential_ams_sweep(R, x, lam, prio_scale=scale)
+        elif blocks is not None:
+            w = block_iterative_sweep(R, x, lam, blocks, prio_scale=scale, norm=norm)
         else:
             w = cimmino_step(R, x, lam, prio_scale=scale, norm=norm)
         log.append(dict(k=k, s=s, accepted=acc, beta=beta_acc, f_start=f_start, f_end=f_x, gnorm=gn))

@@ -536,6 +536,94 @@ def test_sequential_sweep_orthogonal_rows_each_on_bound():
     np.testing.assert_allclose(dose, [1.0, 9.0], rtol=1e-14)
 
 
+# ------------------------------------------------------------ block-iterative sweep (R13)
+
+@pytest.mark.parametrize("norm", ["all", "violated"])
+def test_block_sweep_single_block_is_cimmino(norm):
+    P, rng = _rand_problem(51)
+    R = oracle.constraint_rows(P)
+    x = rng.uniform(0.0, 3.0, P.n_spots)
+    one = [np.arange(R.A.shape[0])]
+    np.testing.assert_allclose(oracle.block_iterative_sweep(R, x, 1.3, one, prio_scale=0.7, norm=norm),
+                               oracle.cimmino_step(R, x, 1.3, prio_scale=0.7, norm=norm), rtol=1e-13, atol=1e-15)
+
+
+def test_block_sweep_singletons_are_the_row_action_sweep():
+    """One row per block with unit priorities is Fig. 2's sweep row by row."""
+    P, rng = _rand_problem(52)
+    for c in P.constraints:
+        c["priority"] = 1.0
+    R = oracle.constraint_rows(P)
+    x = rng.uniform(0.0, 3.0, P.n_spots)
+    singles = [np.array([r]) for r in range(R.A.shape[0])]
+    np.testing.assert_allclose(oracle.block_iterative_sweep(R, x, 1.0, singles),
+                               oracle.sequential_ams_sweep(R, x, 1.0), rtol=1e-13, atol=1e-15)
+
+
+def test_block_sweep_later_block_sees_earlier_update():
+    """Two blocks sharing a spot: the second block projects from the point the
+    first block produced, so its row lands exactly on its bound (lam = 1)."""
+    D = [[1.0, 1.0, 0.0], [0.0, 1.0, 1.0]]
+    cons = [dict(struct_bit=0, kind="DOSE_MAX", bound=1.0, priority=1.0),
+            dict(struct_bit=1, kind="DOSE_MIN", bound=5.0, priority=1.0)]
+    P = small_problem(D, D, [1, 2], cons)
+    R = oracle.constraint_rows(P)
+    x = np.array([1.0, 1.0, 1.0])
+    xn = oracle.block_iterative_sweep(R, x, 1.0, [np.array([0]), np.array([1])])
+    dose, _ = oracle.forward(P, xn)
+    assert abs(dose[1] - 5.0) < 1e-14            # the last projection is exact
+    x1 = x + (1.0 - 2.0) / 2.0 * np.array([1.0, 1.0, 0.0])  # first block by hand
+    x2 = x1 + (5.0 - (x1[1] + x1[2])) / 2.0 * np.array([0.0, 1.0, 1.0])
+    np.testing.assert_allclose(xn, np.maximum(x2, 0.0), rtol=1e-15)
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 1.9])
+def test_block_sweep_fejer_monotone(lam):
+    rng = np.random.default_rng(53)
+    n_vox, n = 16, 6
+    D = rng.uniform(0.05, 1.0, (n_vox, n))
+    L = rng.uniform(1.0, 10.0, (n_vox, n)) * D
+    z = rng.uniform(0.2, 1.0, n)
+    dz, lz = D @ z, L @ z
+    mask = np.ones(n_vox, np.uint32) * 3
+    mask[::3] = 1
+    cons = [dict(struct_bit=0, kind="DOSE_MAX", bound=float(dz.max()) * 1.01, priority=1.0),
+            dict(struct_bit=0, kind="DOSE_MIN", bound=float(dz.min()) * 0.99, priority=2.0),
+            dict(struct_bit=1, kind="LETD_MAX", bound=float((lz / dz).max()) * 1.01, priority=1.0)]
+    P = small_problem(D, L, mask, cons)
+    R = oracle.constraint_rows(P)
+    for trial in range(10):
+        x = rng.uniform(0.0, 4.0, n)
+        for nb in (2, 5, 16):
+            for norm in ("all", "violated"):
+                xn = oracle.block_iterative_sweep(R, x, lam, oracle.sweep_blocks(P, R, nb), norm=norm)
+                assert np.linalg.norm(xn - z) <= np.linalg.norm(x - z) + 1e-12
+
+
+def test_sweep_blocks_group_consecutive_structure_voxels(tiny):
+    pl, P, R = tiny
+    nz = np.diff(pl.row_ptr) > 0
+    C = [v for v in range(pl.n_vox) if pl.mask[v] != 0 and nz[v]]
+    for nb in (1, 3, 7, 64, len(C) + 5):
+        blocks = oracle.sweep_blocks(P, R, nb)
+        S = -(-len(C) // nb)
+        assert len(blocks) == -(-len(C) // S) and len(blocks) <= nb
+        seen = np.concatenate(blocks)
+        assert sorted(seen.tolist()) == list(range(R.A.shape[0]))   # a partition of the rows
+        pos = {v: i for i, v in enumerate(C)}
+        for b, B in enumerate(blocks):
+            for r in B:
+                assert pos[int(R.voxel[r])] // S == b                 # voxel group of S
+
+
+def test_superiorize_with_one_sweep_block_is_plain_superiorize(tiny):
+    pl, P, R = tiny
+    w_a, log_a = oracle.superiorize(P, pl.w0, 4, pl.alpha, pl.relaxation, rows=R)
+    w_b, log_b = oracle.superiorize(P, pl.w0, 4, pl.alpha, pl.relaxation, rows=R, sweep=1)
+    np.testing.assert_allclose(w_b, w_a, rtol=1e-12, atol=1e-14)
+    assert [e["s"] for e in log_a] == [e["s"] for e in log_b]
+
+
 # ------------------------------------------------------------ inputs
 
 def test_philox_known_answers():
