@@ -105,7 +105,13 @@ typedef struct fredopt_params {
   double c_cdl;           /* c of cDL = c * dose * LETd, um/keV (default 0.04, Sec. 2.4) */
   int32_t log_capacity;   /* per-iteration log entries kept on the device (default 4096) */
   int32_t use_graphs;     /* 1: replay iterations as CUDA graphs (default); 0: plain launches */
+  int32_t sweep_blocks;   /* 0 (default): simultaneous feasibility step (Cimmino).  M in
+                             1..FREDOPT_MAX_SWEEP_BLOCKS: block-iterative sweep of Fig. 2 over M
+                             voxel blocks (see fredopt_sweep_step) */
+  int32_t reserved;       /* 0 */
 } fredopt_params;
+
+#define FREDOPT_MAX_SWEEP_BLOCKS 1024
 
 typedef struct fredopt_log_entry {
   int64_t k;           /* iteration index */
@@ -223,6 +229,22 @@ int fredopt_backward(fredopt_t h, const float* a_D, const float* a_L, float* u_o
  * Needs constraints.  norm = FREDOPT_NORM_*. */
 int fredopt_feasibility_step(fredopt_t h, const float* x, double relaxation, double prio_scale,
                              int norm, float* w_out, uint32_t flags);
+
+/* One block-iterative sweep from x: the block-iterative form of Fig. 2's
+ * row-action sweep.  The voxels that lie in some structure and have
+ * influence entries are taken in ascending voxel order and grouped into
+ * blocks of S = ceil(count / n_blocks) consecutive voxels (the last block may
+ * be smaller; fewer than n_blocks blocks when count < n_blocks); all
+ * constraint rows of a voxel share its block.  Blocks are visited in order;
+ * inside a block the rows are projected simultaneously from the block's
+ * starting point,
+ *   x <- x + relaxation * prio_scale * sum_{r in B} (p_r / W_B) t_r a_r,
+ * with W_B the priority sum of the block's reachable rows (norm ALL) or of its
+ * violated rows (norm VIOLATED); after the last block w_out = max(0, x).
+ * n_blocks = 1 is the simultaneous step; one voxel per block approaches the
+ * row-action sweep.  1 <= n_blocks <= FREDOPT_MAX_SWEEP_BLOCKS. */
+int fredopt_sweep_step(fredopt_t h, const float* x, double relaxation, double prio_scale, int norm,
+                       int n_blocks, float* w_out, uint32_t flags);
 
 /* Objective f(x) (Eq. 2 terms, FP64 reduction) and its gradient g (float[n_spots]). */
 int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_out, uint32_t flags);

@@ -104,6 +104,16 @@ struct fredopt_ctx {
   DBuf<double2> y64;
   DBuf<float> chunk_sum, fout_a, fout_b, vin_a, vin_b;
   DBuf<uint8_t> vol_buf;  // volume statistics scratch
+
+  // block-iterative sweep (built for sweep_m requested blocks; 0 = not built)
+  int sweep_m = 0;
+  int sweep_nb = 0;                          // blocks actually formed
+  std::vector<int64_t> h_sweep_bounds;       // [sweep_nb + 1] device rows
+  std::vector<int64_t> sweep_wr_off;         // [sweep_nb] offset (in pairs) of each block's warp ranges
+  std::vector<int> sweep_warps;              // [sweep_nb] warps of each block's forward product
+  DBuf<int64_t> sweep_wr, sweep_pos, sweep_bounds_d;
+  DBuf<float> xs;                            // the point being swept [n_pad]
+  DBuf<float2> ys;                           // forward product of the block rows [n_hot]
   DBuf<double> part;
   DBuf<DevState> st;
   DBuf<LogEntry> log;
@@ -379,6 +389,97 @@ ConArgs con_args(fredopt_t h) {
   return c;
 }
 
+
+// Blocks of the block-iterative sweep: the streamed rows with nonzeros that
+// lie in some structure, in device (= ascending voxel) order, cut into groups
+// of S = ceil(count / m) rows; block t covers the device rows from its first
+// structure row to the next block's first.  Builds each block's forward
+// schedule and the CSC position table of the block boundaries.
+int build_sweep(fredopt_t h, int m) {
+  if (h->sweep_m == m) return FREDOPT_OK;
+  cudaStream_t s = h->stream;
+  std::vector<int64_t> C;
+  for (int64_t r = 0; r < h->n_hot_ne; ++r)
+    if (h->h_mask[r] != 0) C.push_back(r);
+  h->h_sweep_bounds.clear();
+  h->sweep_wr_off.clear();
+  h->sweep_warps.clear();
+  h->sweep_nb = 0;
+  if (!C.empty()) {
+    const int64_t S = ((int64_t)C.size() + m - 1) / m;
+    const int nb = (int)(((int64_t)C.size() + S - 1) / S);
+    for (int t = 0; t < nb; ++t) h->h_sweep_bounds.push_back(C[(size_t)t * S]);
+    h->h_sweep_bounds.push_back(C.back() + 1);
+    h->sweep_nb = nb;
+  }
+  std::vector<int64_t> wr;
+  for (int t = 0; t < h->sweep_nb; ++t) {
+    const int64_t r0 = h->h_sweep_bounds[t], r1 = h->h_sweep_bounds[t + 1];
+    const int warps = (int)std::max<int64_t>(1, std::min<int64_t>(h->geo.fwd_warps, r1 - r0));
+    const std::vector<int64_t> p = partition_pairs(h->h_rp, {{r0, r1}}, warps, h->row_cost);
+    h->sweep_wr_off.push_back((int64_t)wr.size() / 2);
+    h->sweep_warps.push_back(warps);
+    wr.insert(wr.end(), p.begin(), p.end());
+  }
+  if (wr.empty()) wr.assign(2, 0);
+  CK(upload_vec(h, h->sweep_wr, wr));
+  const int nbnd = h->sweep_nb + 1;
+  std::vector<int64_t> bnd = h->h_sweep_bounds;
+  if (bnd.empty()) bnd.assign(1, 0);
+  CK(upload_vec(h, h->sweep_bounds_d, bnd));
+  CK(h->sweep_pos.alloc((size_t)std::max(1, nbnd) * h->n));
+  if (h->sweep_nb > 0) launch_sweep_pos(h->cp.p, h->crow.p, h->n, h->sweep_bounds_d.p, nbnd, h->sweep_pos.p, s);
+  CK(h->xs.ensure(h->n_pad));
+  CK(cudaMemsetAsync(h->xs.p, 0, h->n_pad * sizeof(float), s));
+  CK(h->ys.ensure(std::max<int64_t>(1, h->n_hot)));
+  CK(cudaMemsetAsync(h->ys.p, 0, std::max<int64_t>(1, h->n_hot) * sizeof(float2), s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  h->sweep_m = m;
+  return FREDOPT_OK;
+}
+
+// One block-iterative sweep from x = w + coef * g (use_coef) or x = w, into out.
+void enqueue_sweep(fredopt_t h, const float* w, int use_coef, double lam, double prio_scale, int norm,
+                   int in_solve, float* out) {
+  const Geometry& G = h->geo;
+  cudaStream_t s = h->stream;
+  run(h, 5, [&] { launch_sweep_start(h->n, w, h->g.p, use_coef, h->xs.p, h->st.p, s); });
+  for (int t = 0; t < h->sweep_nb; ++t) {
+    FwdArgs fa = fwd_args(h, true);
+    fa.warp_row = h->sweep_wr.p + 2 * h->sweep_wr_off[t];
+    fa.n_warps = h->sweep_warps[t];
+    fa.x = h->xs.p;
+    fa.y = h->ys.p;
+    run(h, 0, [&] { launch_forward(G, h->fmt, EPI_STORE, h->hint_fwd, fa, h->tab, s); });
+    ConArgs k2 = con_args(h);
+    k2.yw = h->ys.p;
+    k2.yg = nullptr;
+    k2.use_coef = 0;
+    k2.r0 = h->h_sweep_bounds[t];
+    k2.n_hot = h->h_sweep_bounds[t + 1];
+    run(h, 2, [&] { launch_constraints(G, h->tab, k2, s); });
+    SweepArgs sa{};
+    sa.pos0 = h->sweep_pos.p + (size_t)t * h->n;
+    sa.pos1 = h->sweep_pos.p + (size_t)(t + 1) * h->n;
+    sa.row = h->crow.p;
+    sa.Dv = h->DTv.p;
+    sa.Lv = h->LTv.p;
+    sa.gam = h->gam.p;
+    sa.x = h->xs.p;
+    sa.n = h->n;
+    sa.k2part = h->part.p + h->off_k2;
+    sa.k2_blocks = G.row_blocks;
+    sa.norm = norm;
+    sa.lam = lam;
+    sa.prio_scale = prio_scale;
+    sa.in_solve = in_solve;
+    sa.st = h->st.p;
+    run(h, 1, [&] { launch_sweep_update(G, h->fmt, sa, s); });
+  }
+  run(h, 3, [&] { launch_sweep_finish(G, h->n, h->xs.p, out, in_solve, h->st.p, h->log.p, s); });
+}
+
 // One superiorized iteration (Fig. 3 around the simultaneous Fig. 2).
 void enqueue_iteration(fredopt_t h) {
   const Geometry& G = h->geo;
@@ -422,6 +523,10 @@ void enqueue_iteration(fredopt_t h) {
     }
   } else {
     run(h, 0, [&] { launch_forward(G, h->fmt, EPI_STORE, h->hint_fwd, fa, t, s); });
+  }
+  if (h->prm.sweep_blocks > 0 && t.n_con > 0) {
+    enqueue_sweep(h, h->w.p, pert ? 1 : 0, h->lam, 1.0, h->prm.cimmino_norm, 1, h->w.p);
+    return;
   }
   ConArgs k2 = con_args(h);
   k2.yg = pert ? h->yg.p : nullptr;
@@ -653,6 +758,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   free_graph(h);
   h->loaded = false;
   h->begun = false;
+  h->sweep_m = 0;
   int rc = FREDOPT_OK;
   cudaStream_t s = h->stream;
   join_in(h);
@@ -897,7 +1003,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   h->off_bc = h->off_f + std::max(G.fwd_warps, G.row_blocks);
   h->off_g = h->off_bc + 2 * G.fwd_warps;
   h->off_k2 = h->off_g + G.col_blocks;
-  h->off_fin = h->off_k2 + 3 * G.row_blocks;
+  h->off_fin = h->off_k2 + 4 * G.row_blocks;
   h->off_cnt = h->off_fin + 8 * G.row_blocks;
   h->n_part = h->off_cnt + 3 * G.row_blocks;
   CK(h->part.alloc(h->n_part));
@@ -994,7 +1100,8 @@ int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
   if (!(p.eta > 0.0 && p.eta <= 1.0)) return fail(h, FREDOPT_ERR_INVALID_ARG, "need 0 < eta <= 1");
   if (p.reductions < 0 || p.max_trials < 1 || p.log_capacity < 0 ||
       (p.cimmino_norm != FREDOPT_NORM_ALL && p.cimmino_norm != FREDOPT_NORM_VIOLATED) ||
-      !(p.c_cdl > 0.0) || !std::isfinite(p.beta0))
+      !(p.c_cdl > 0.0) || !std::isfinite(p.beta0) || p.sweep_blocks < 0 ||
+      p.sweep_blocks > FREDOPT_MAX_SWEEP_BLOCKS)
     return fail(h, FREDOPT_ERR_INVALID_ARG, "bad parameters");
   DeviceGuard dg(h->device);
   cudaStream_t s = h->stream;
@@ -1013,6 +1120,10 @@ int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
     nrm += (double)v * (double)v;
   }
   free_graph(h);
+  if (p.sweep_blocks > 0) {
+    rc = build_sweep(h, p.sweep_blocks);
+    if (rc) return rc;
+  }
   h->prm = p;
   h->alpha = alpha;
   h->lam = relaxation;
@@ -1331,6 +1442,32 @@ int fredopt_feasibility_step(fredopt_t h, const float* x, double relaxation, dou
   run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
   CK(cudaGetLastError());
   CK(copy_out(h, w_out, h->xbuf.p, (size_t)h->n * sizeof(float), flags));
+  rc = check_sticky(h);
+  collect_timers(h);
+  return rc;
+}
+
+int fredopt_sweep_step(fredopt_t h, const float* x, double relaxation, double prio_scale, int norm,
+                       int n_blocks, float* w_out, uint32_t flags) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (!x || !w_out) return fail(h, FREDOPT_ERR_INVALID_ARG, "null x or w_out");
+  if (!(relaxation > 0.0 && relaxation <= 2.0)) return fail(h, FREDOPT_ERR_INVALID_ARG, "need 0 < relaxation <= 2");
+  if (norm != FREDOPT_NORM_ALL && norm != FREDOPT_NORM_VIOLATED) return fail(h, FREDOPT_ERR_INVALID_ARG, "bad norm");
+  if (n_blocks < 1 || n_blocks > FREDOPT_MAX_SWEEP_BLOCKS)
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "need 1 <= n_blocks <= FREDOPT_MAX_SWEEP_BLOCKS");
+  if (h->begun && h->gexec && h->prm.sweep_blocks > 0 && h->sweep_m != n_blocks)
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "the begun solve sweeps another number of blocks");
+  DeviceGuard dg(h->device);
+  join_in(h);
+  rc = build_sweep(h, n_blocks);
+  if (rc) return rc;
+  rc = load_spot_vec(h, h->xbuf, x, flags);
+  if (rc) return rc;
+  CK(h->gtmp.ensure(h->n_pad));
+  enqueue_sweep(h, h->xbuf.p, 0, relaxation, prio_scale, norm, 0, h->gtmp.p);
+  CK(cudaGetLastError());
+  CK(copy_out(h, w_out, h->gtmp.p, (size_t)h->n * sizeof(float), flags));
   rc = check_sticky(h);
   collect_timers(h);
   return rc;

@@ -60,6 +60,7 @@ struct DevState {
   int err;            // bit 0: bulk-copy wait timed out
   unsigned int done;  // last-block counter of the column finish
   int pad;
+  double sweep_nv, sweep_mx;  // block-iterative sweep: violated rows and largest violation
 };
 
 struct LogEntry {
@@ -140,9 +141,10 @@ struct ConArgs {
   const double* dl;
   const float* sD;
   const float* sL;
+  int64_t r0;           // rows [r0, n_hot) are evaluated (0 for the whole set)
   int64_t n_hot;
   float2* gam;
-  double* part;         // per-block: [sum p violated, n violated, max violation]
+  double* part;         // per-block: [sum p violated, n violated, max violation, sum p reachable]
   int32_t use_coef;
   DevState* st;
 };
@@ -216,6 +218,33 @@ void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_
                         cudaStream_t s);
 void launch_scale_coef(int64_t n, const float* aD, const float* aL, const int64_t* voxel,
                        const float* sD, const float* sL, float2* coef, cudaStream_t s);
+
+// ---- block-iterative sweep (fredopt_sweep.cu)
+struct SweepArgs {
+  const int64_t* pos0;   // [n]: first CSC position of each column at or after the block's first row
+  const int64_t* pos1;   // [n]: same for the next block
+  const int32_t* row;    // CSC row indices (streamed rows)
+  const void* Dv;        // CSC values
+  const void* Lv;
+  const float2* gam;     // per streamed row (scaled like the transposed product's coefficients)
+  float* x;              // [n], updated in place
+  int32_t n;
+  const double* k2part;  // constraint partials of the block (4 slices of k2_blocks)
+  int32_t k2_blocks;
+  int32_t norm;
+  double lam;
+  double prio_scale;     // outside a solve
+  int32_t in_solve;      // 1: scale eta^k from DevState and count the block's violations
+  DevState* st;
+};
+
+void launch_sweep_start(int n, const float* w, const float* g, int use_coef, float* x, DevState* st,
+                        cudaStream_t s);
+void launch_sweep_pos(const int64_t* cp, const int32_t* row, int32_t n, const int64_t* bounds, int n_bounds,
+                      int64_t* pos, cudaStream_t s);
+void launch_sweep_update(const Geometry& g, int fmt, const SweepArgs& a, cudaStream_t s);
+void launch_sweep_finish(const Geometry& g, int n, const float* x, float* out, int in_solve, DevState* st,
+                         LogEntry* log, cudaStream_t s);
 
 // ---- volume statistics (fredopt_volume.cu)
 constexpr int kMaxVolReq = 64;  // requests per call

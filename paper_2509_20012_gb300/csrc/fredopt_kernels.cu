@@ -23,6 +23,8 @@
 //                    blocked stable counting transpose (CSR -> CSC).
 #include "fredopt_internal.cuh"
 
+#include <algorithm>
+
 #include <cstdio>
 #include <type_traits>
 
@@ -595,11 +597,11 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
 
 __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t) {
   __shared__ double red[kRowThreads];
-  const int64_t per = (a.n_hot + gridDim.x - 1) / gridDim.x;
-  const int64_t i0 = (int64_t)blockIdx.x * per;
+  const int64_t per = (a.n_hot - a.r0 + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = a.r0 + (int64_t)blockIdx.x * per;
   const int64_t i1 = min(a.n_hot, i0 + per);
   const double coef = a.use_coef ? a.st->coef : 0.0;
-  double psum = 0.0, nv = 0.0, mx = 0.0;
+  double psum = 0.0, nv = 0.0, mx = 0.0, preach = 0.0;
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const uint32_t m = a.mask[i];
     float2 out = make_float2(0.f, 0.f);
@@ -627,6 +629,7 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
           b = 0.0;
         }
         if (!(n2 > 0.0)) continue;  // unreachable row
+        preach += c.prio;
         const bool upper = (c.kind & 1) != 0;
         const double viol = upper ? v - b : b - v;
         if (viol > 0.0) {
@@ -649,10 +652,12 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
   psum = block_sum256(psum, red);
   nv = block_sum256(nv, red);
   mx = block_max256(mx, red);
+  preach = block_sum256(preach, red);
   if (threadIdx.x == 0) {
     a.part[blockIdx.x] = psum;
     a.part[gridDim.x + blockIdx.x] = nv;
     a.part[2 * gridDim.x + blockIdx.x] = mx;
+    a.part[3 * gridDim.x + blockIdx.x] = preach;
   }
 }
 
@@ -1295,6 +1300,145 @@ int init_kernels(Geometry* g, int device) {
   if (set_smem_all<__nv_bfloat16>(bytes) != cudaSuccess) return -2;
   if (set_smem_all<__half>(bytes) != cudaSuccess) return -2;
   return 0;
+}
+
+// ------------------------------------------------------------------ block-iterative sweep
+
+// x = w + coef * g (the perturbed point; coef = 0 without perturbation), and
+// the sweep's violation counters cleared.
+__global__ void k_sweep_start(int n, const float* __restrict__ w, const float* __restrict__ g, int use_coef,
+                              float* __restrict__ x, DevState* st) {
+  const double coef = use_coef ? st->coef : 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    x[j] = use_coef ? (float)((double)w[j] + coef * (double)g[j]) : w[j];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->sweep_nv = 0.0;
+    st->sweep_mx = 0.0;
+  }
+}
+
+// pos[t * n + j] = first CSC position of column j whose row is >= bounds[t].
+__global__ void k_sweep_pos(const int64_t* __restrict__ cp, const int32_t* __restrict__ row, int32_t n,
+                            const int64_t* __restrict__ bounds, int n_bounds, int64_t* __restrict__ pos) {
+  const int64_t total = (int64_t)n_bounds * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(idx / n);
+    const int j = (int)(idx - (int64_t)t * n);
+    const int64_t target = bounds[t];
+    int64_t lo = cp[j], hi = cp[j + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)row[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    pos[idx] = lo;
+  }
+}
+
+// One block of the sweep: u_j = sum over the block's CSC entries of column j
+// of D_ij gamma_D[i] + L_ij gamma_L[i] (one warp per column, fixed order), then
+// x_j += lam * scale / W_B * u_j.  W_B and the violation counts come from the
+// block's constraint partials.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_sweep_update(SweepArgs a) {
+  __shared__ double red[256];
+  __shared__ double sh_scale;
+  const double W = block_sum_array(a.k2part + (a.norm == 1 ? 0 : 3 * a.k2_blocks), a.k2_blocks, red);
+  if (a.in_solve && blockIdx.x == 0) {
+    const double nv = block_sum_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
+    const double mx = block_max_array(a.k2part + 2 * a.k2_blocks, a.k2_blocks, red);
+    if (threadIdx.x == 0) {
+      a.st->sweep_nv += nv;
+      a.st->sweep_mx = fmax(a.st->sweep_mx, mx);
+    }
+  }
+  if (threadIdx.x == 0) {
+    const double ps = a.in_solve ? pow(a.st->eta, (double)a.st->k) : a.prio_scale;
+    sh_scale = W > 0.0 ? a.lam * ps / W : 0.0;
+  }
+  __syncthreads();
+  const double scale = sh_scale;
+  if (scale == 0.0) return;
+  const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
+  const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < a.n; j += nw) {
+    const int64_t p0 = a.pos0[j], p1 = a.pos1[j];
+    if (p1 <= p0) continue;
+    float acc = 0.0f;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const float2 c = a.gam[a.row[p]];
+      acc = fmaf(to_f(Dv[p]), c.x, acc);
+      acc = fmaf(to_f(Lv[p]), c.y, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) a.x[j] = (float)((double)a.x[j] + scale * (double)acc);
+  }
+}
+
+// out = max(0, x); in a solve the last block writes the log entry and advances k.
+__global__ void __launch_bounds__(256) k_sweep_finish(int n, const float* __restrict__ x, float* __restrict__ out,
+                                                      int in_solve, DevState* st, LogEntry* log) {
+  __shared__ bool sh_last;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    out[j] = x[j] > 0.0f ? x[j] : 0.0f;
+  if (!in_solve) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->done, 1u);
+    sh_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (sh_last && threadIdx.x == 0) {
+    __threadfence();
+    if (st->log_cap > 0) {
+      LogEntry e;
+      e.k = st->k;
+      e.s = st->s;
+      e.accepted = st->accepted;
+      e.n_violated = (int)st->sweep_nv;
+      e.beta = st->beta_acc;
+      e.f_start = st->f_start;
+      e.f_end = st->f_cur;
+      e.gnorm = st->gnorm;
+      e.max_violation = st->sweep_mx;
+      log[st->k % st->log_cap] = e;
+    }
+    st->k += 1;
+    st->done = 0u;
+  }
+}
+
+void launch_sweep_start(int n, const float* w, const float* g, int use_coef, float* x, DevState* st,
+                        cudaStream_t s) {
+  k_sweep_start<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, s>>>(n, w, g, use_coef, x, st);
+}
+
+void launch_sweep_pos(const int64_t* cp, const int32_t* row, int32_t n, const int64_t* bounds, int n_bounds,
+                      int64_t* pos, cudaStream_t s) {
+  const int64_t total = (int64_t)n_bounds * n;
+  if (total == 0) return;
+  const unsigned gb = (unsigned)std::min<int64_t>((total + 255) / 256, 65535);
+  k_sweep_pos<<<gb, 256, 0, s>>>(cp, row, n, bounds, n_bounds, pos);
+}
+
+void launch_sweep_update(const Geometry& g, int fmt, const SweepArgs& a, cudaStream_t s) {
+  const unsigned gb = (unsigned)std::max(1, std::min(g.n_sms * 8, (a.n + 7) / 8));
+  if (fmt == 1)
+    k_sweep_update<__nv_bfloat16><<<gb, 256, 0, s>>>(a);
+  else if (fmt == 2)
+    k_sweep_update<__half><<<gb, 256, 0, s>>>(a);
+  else
+    k_sweep_update<float><<<gb, 256, 0, s>>>(a);
+}
+
+void launch_sweep_finish(const Geometry& g, int n, const float* x, float* out, int in_solve, DevState* st,
+                         LogEntry* log, cudaStream_t s) {
+  const unsigned gb = (unsigned)std::max(1, std::min(g.n_sms, (n + 255) / 256));
+  k_sweep_finish<<<gb, 256, 0, s>>>(n, x, out, in_solve, st, log);
 }
 
 }  // namespace fo

@@ -24,6 +24,7 @@ ROWS = {"all": 0x000, "roi": 0x100}
 KINDS = {"DOSE_MIN": 0, "DOSE_MAX": 1, "CDL_MIN": 2, "CDL_MAX": 3, "LETD_MIN": 4, "LETD_MAX": 5}
 QUANTITIES = {"DOSE": 0, "CDL": 1, "LETD": 2}  # LETD: volume statistics only
 VOLUME_MAX_REQUESTS, VOLUME_MAX_BINS, VOLUME_MAX_FRACS = 64, 16384, 64
+MAX_SWEEP_BLOCKS = 1024
 NORMS = {"all": 0, "violated": 1}
 KCLASS_N = 6
 KCLASS_NAMES = ["forward", "backward", "constraints", "colfinish", "finish", "other"]
@@ -50,7 +51,7 @@ class Params(ctypes.Structure):
                 ("reductions", ctypes.c_int32), ("max_trials", ctypes.c_int32),
                 ("cimmino_norm", ctypes.c_int32), ("grad_normalize", ctypes.c_int32),
                 ("c_cdl", ctypes.c_double), ("log_capacity", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("sweep_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class LogEntry(ctypes.Structure):
@@ -136,6 +137,8 @@ _SIGS = {
                                         ctypes.c_uint32]),
     "fredopt_feasibility_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32]),
+    "fredopt_sweep_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32]),
     "fredopt_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_void_p, ctypes.c_uint32]),
     "fredopt_volume_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int,
@@ -402,6 +405,15 @@ class Handle:
         self._check(self.lib.fredopt_feasibility_step(self.h, _ptr(x, np.float32)[0], float(relaxation),
                                                       float(prio_scale), NORMS[norm], _ptr(w, np.float32)[0],
                                                       DEVICE_PTR if dev else 0))
+        return w
+
+    def sweep_step(self, x, n_blocks, relaxation=1.0, prio_scale=1.0, norm="all"):
+        """One block-iterative sweep of Fig. 2 over n_blocks voxel blocks from x."""
+        dev = _on_device(x)
+        w = self._out(dev, self.n_spots)
+        self._check(self.lib.fredopt_sweep_step(self.h, _ptr(x, np.float32)[0], float(relaxation),
+                                                float(prio_scale), NORMS[norm], int(n_blocks),
+                                                _ptr(w, np.float32)[0], DEVICE_PTR if dev else 0))
         return w
 
     def objective(self, x):
