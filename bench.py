@@ -289,6 +289,10 @@ def run_gpu_arm(args):
                "what": f"load_influence from pinned host + set_constraints + set_objective + "
                        f"superiorize({args.e2e_iters} iters) with host w0/w/dose/LETd; {t_e2e:.3f} s"}
 
+    sweep = None
+    if rank == 0 and args.sweep:
+        sweep = sweep_benchmark(plan, local, stream)
+
     volume = None
     if rank == 0 and args.volume:
         volume = volume_benchmark(plan, main["w"], local, stream, hbm)
@@ -331,6 +335,8 @@ def run_gpu_arm(args):
         }
         if volume is not None:
             line["volume_stats"] = volume
+        if sweep is not None:
+            line["sweep"] = sweep
         if serving is not None:
             line["serving"] = serving
         if batching is not None:
@@ -579,6 +585,46 @@ def volume_benchmark(plan, w, local, stream, hbm, reps=20):
     return out
 
 
+def sweep_benchmark(plan, local, stream, iters=100, warmup=5):
+    """Superiorized iterations with the block-iterative feasibility sweep
+    (sweep_blocks voxel blocks visited in turn) against the simultaneous step,
+    clinical plan in ROI-row mode (the sweep's blocks are structure voxels)."""
+    import torch
+    from paper_2509_20012_gb300 import Handle
+    out = {}
+    for m in (0, 16, 64, 256):
+        h = Handle(local, stream=stream)
+        h.load_plan(plan, rows="roi")
+        h.begin(plan.w0, plan.alpha, plan.relaxation, sweep_blocks=m)
+        h.iterate(warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.iterate(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches_per_iter = None
+        _, _, _, rep = h.end()
+        # per-class device time from a short run with events around every launch
+        h.set_timing(True)
+        h.begin(plan.w0, plan.alpha, plan.relaxation, sweep_blocks=m)
+        n0 = h.launch_count()
+        h.iterate(10)
+        torch.cuda.synchronize()
+        launches_per_iter = (h.launch_count() - n0) / 10
+        kt = h.get_timing()
+        h.close()
+        out["simultaneous" if m == 0 else f"sweep{m}"] = {
+            "iters_per_s": iters / (ms * 1e-3), "ms_per_iter": ms / iters, "launches_per_iter": launches_per_iter,
+            "kernel_ms_per_iter": {k: v[0] / 10 for k, v in kt.items()},
+            "max_violation_after": rep["max_violation"], "n_violated_after": rep["n_violated"]}
+    out["note"] = (f"clinical plan, ROI rows, {iters} superiorized iterations after {warmup} warm-up, CUDA graph "
+                   "replay; kernel_ms_per_iter from a 10-iteration run with events around every launch "
+                   "(sweep: forward = block forward products, backward = block column updates)")
+    return out
+
+
 def cpu_baseline(plan, iters):
     """FP64 oracle, as it stands, on `iters` iterations of the same plan."""
     import oracle
@@ -649,6 +695,8 @@ def main():
                     help="skip the batching workloads in the default run")
     ap.add_argument("--no-robust", dest="robust", action="store_false")
     ap.add_argument("--batch-iters", type=int, default=100)
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip the block-iterative sweep timing")
     ap.add_argument("--no-volume", dest="volume", action="store_false",
                     help="skip the volume-statistics timing (DVH, values at volume)")
     args = ap.parse_args()

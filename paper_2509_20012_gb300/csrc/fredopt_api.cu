@@ -458,7 +458,10 @@ void enqueue_sweep(fredopt_t h, const float* w, int use_coef, double lam, double
     k2.use_coef = 0;
     k2.r0 = h->h_sweep_bounds[t];
     k2.n_hot = h->h_sweep_bounds[t + 1];
-    run(h, 2, [&] { launch_constraints(G, h->tab, k2, s); });
+    // one CTA per 256 rows of the block, at most the usual grid
+    const int k2_grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(G.row_blocks, (k2.n_hot - k2.r0 + 255) / 256));
+    run(h, 2, [&] { launch_constraints(G, h->tab, k2, s, k2_grid); });
     SweepArgs sa{};
     sa.pos0 = h->sweep_pos.p + (size_t)t * h->n;
     sa.pos1 = h->sweep_pos.p + (size_t)(t + 1) * h->n;
@@ -469,7 +472,7 @@ void enqueue_sweep(fredopt_t h, const float* w, int use_coef, double lam, double
     sa.x = h->xs.p;
     sa.n = h->n;
     sa.k2part = h->part.p + h->off_k2;
-    sa.k2_blocks = G.row_blocks;
+    sa.k2_blocks = k2_grid;
     sa.norm = norm;
     sa.lam = lam;
     sa.prio_scale = prio_scale;

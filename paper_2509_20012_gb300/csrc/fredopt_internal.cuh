@@ -175,7 +175,8 @@ void launch_forward(const Geometry& g, int fmt, int epi, bool stream_hint, const
 void launch_backward(const Geometry& g, int fmt, bool stream_hint, bool use_D, const BwdArgs& a,
                      cudaStream_t s);
 void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_t s);
-void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s);
+// grid 0: g.row_blocks CTAs (the partials' stride); otherwise that many
+void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s, int grid = 0);
 void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
                    const double* part_g, int ng, DevState* st, cudaStream_t s);
 void launch_count_rows(const Geometry& g, const Tables& t, const uint32_t* mask, const double* dd,

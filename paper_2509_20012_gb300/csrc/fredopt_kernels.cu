@@ -1030,7 +1030,10 @@ __global__ void k_scatter_y(const float2* y, const int64_t* voxel, int64_t n, fl
 template <typename VT, int EPI, bool XS, bool S>
 static void fwd_inst(const Geometry& g, const FwdArgs& a, const Tables& t, cudaStream_t s) {
   const size_t smem = XS ? (size_t)a.n_x_pad * sizeof(float) + 16 : 0;
-  k_forward<VT, EPI, XS, S><<<g.fwd_blocks, g.fwd_threads, smem, s>>>(a, t);
+  // only the CTAs that hold scheduled warps (all of them for a full pass)
+  const int wpb = g.fwd_threads / 32;
+  const int blocks = std::max(1, std::min(g.fwd_blocks, (a.n_warps + wpb - 1) / wpb));
+  k_forward<VT, EPI, XS, S><<<blocks, g.fwd_threads, smem, s>>>(a, t);
 }
 
 template <typename VT, int EPI>
@@ -1097,8 +1100,8 @@ void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_
   else k_colfinish<COL_PROJ><<<g.col_blocks, kColThreads, 0, s>>>(a);
 }
 
-void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s) {
-  k_constraints<<<g.row_blocks, kRowThreads, 0, s>>>(a, t);
+void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s, int grid) {
+  k_constraints<<<grid > 0 ? grid : g.row_blocks, kRowThreads, 0, s>>>(a, t);
 }
 
 void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
