@@ -911,7 +911,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   // ---- CSC copy of the streamed rows (blocked stable counting transpose)
   {
     // rows without nonzeros (after the others in device order) add nothing
-    const int n_blk = (int)std::max<int64_t>(1, std::min<int64_t>(2 * h->geo.n_sms, n_hot_ne));
+    const int n_blk = (int)std::max<int64_t>(1, std::min<int64_t>(h->geo.n_sms, n_hot_ne));  // one wave of 1024-thread blocks
     std::vector<int64_t> blk = partition_rows(rpd, n_hot_ne, n_blk, 1);
     DBuf<int64_t> blk_d, tot_d;
     DBuf<int32_t> cnt;
@@ -938,11 +938,15 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(cudaMemsetAsync(h->crow.p + h->nnz_hot, 0, (nh_alloc - h->nnz_hot) * sizeof(int32_t), s));
     CK(cudaMemsetAsync(h->DTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
     CK(cudaMemsetAsync(h->LTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
+    CK(cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
     if (n_hot_ne > 0)
-      launch_csc_fill(fmt, h->rp.p, h->col.p, h->Dv.p, h->Lv.p, blk_d.p, n_blk, n_spots, cnt.p,
-                      h->crow.p, h->DTv.p, h->LTv.p, s);
+      launch_csc_fill(h->geo, fmt, h->rp.p, h->col.p, h->Dv.p, h->Lv.p, blk_d.p, n_blk, n_spots, cnt.p,
+                      h->crow.p, h->DTv.p, h->LTv.p, h->errw.p, s);
     CK(cudaGetLastError());
+    int ferr = 0;
+    CK(cudaMemcpyAsync(&ferr, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (ferr) return fail(h, FREDOPT_ERR_TIMEOUT, "a bounded device-side wait gave up (CSC transpose)");
 
     // chunk schedule of the transposed product
     const int W3 = h->geo.bwd_warps;

@@ -901,12 +901,22 @@ __global__ void k_moments(const int64_t* rp, int64_t n_rows, const VT* Dv, const
 }
 
 // blocked counting transpose: block b owns rows [blk_row[b], blk_row[b+1])
-__global__ void k_csc_count(const int64_t* rp, const int32_t* col, const int64_t* blk_row,
-                            int32_t n_cols, int32_t* cnt) {
+template <bool SMEM>
+__global__ void k_csc_count(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const int64_t* __restrict__ blk_row, int32_t n_cols, int32_t* __restrict__ cnt) {
+  extern __shared__ int32_t sh_cnt[];
   const int b = blockIdx.x;
   const int64_t s = rp[blk_row[b]], e = rp[blk_row[b + 1]];
   int32_t* c = cnt + (int64_t)b * n_cols;
-  for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) atomicAdd(&c[col[p]], 1);
+  if (SMEM) {  // a shared-memory histogram, then one coalesced write of the block's row
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) sh_cnt[j] = 0;
+    __syncthreads();
+    for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) atomicAdd(&sh_cnt[col[p]], 1);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) c[j] = sh_cnt[j];
+  } else {
+    for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) atomicAdd(&c[col[p]], 1);
+  }
 }
 
 __global__ void k_csc_colsum(const int32_t* cnt, int n_blk, int32_t n_cols, int64_t* tot) {
@@ -933,30 +943,130 @@ __global__ void k_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int
 // Rows of a block in ascending order; within a row all columns differ, so
 // the cursor updates of one row never collide; a barrier separates rows,
 // which keeps the rows of every column ascending (a stable transpose).
+// The block's nonzeros reach shared memory by bulk copies (TMA engine) in
+// windows of W elements, two buffers deep: while the rows of one window are
+// scattered the next window is in flight, and a block barrier does not wait
+// for bulk copies, so a row costs shared-memory reads, a cursor update and a
+// barrier.  Row pointers are staged in chunks of kFillRows rows.  A bounded
+// wait that gives up sets bit 0 of *err; the block lets its copies land and
+// stops (the load then fails with a timeout).
+constexpr int kFillThreads = 1024;
+constexpr int kFillRows = 2048;
+constexpr int64_t kFillAlign = 8;  // window starts and lengths: 16 bytes of every array
+constexpr size_t kFillRpBytes = ((kFillRows + 1) * sizeof(int64_t) + 15) & ~(size_t)15;
+
+template <typename VT>
+size_t csc_fill_smem(int W, int32_t n_cols, bool smem_cursors) {
+  return 2 * (size_t)W * (sizeof(int32_t) + 2 * sizeof(VT)) + kFillRpBytes +
+         (smem_cursors ? (((size_t)n_cols * sizeof(int32_t) + 15) & ~(size_t)15) : 0) + 2 * sizeof(uint64_t);
+}
+
 template <typename VT, bool SMEM>
-__global__ void k_csc_fill(const int64_t* rp, const int32_t* col, const VT* Dv, const VT* Lv,
-                           const int64_t* blk_row, int32_t n_cols, int32_t* cursor, int32_t* row_out,
-                           VT* DT, VT* LT) {
-  extern __shared__ int32_t sh_cur[];
+__global__ void __launch_bounds__(kFillThreads) k_csc_fill(
+    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ Dv,
+    const VT* __restrict__ Lv, const int64_t* __restrict__ blk_row, int32_t n_cols, int32_t* __restrict__ cursor,
+    int32_t* __restrict__ row_out, VT* __restrict__ DT, VT* __restrict__ LT, int W, int* err) {
+  extern __shared__ __align__(16) unsigned char fill_sh[];
   const int b = blockIdx.x;
+  const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
+  if (r0 >= r1) return;
+  const size_t win_bytes = (size_t)W * (sizeof(int32_t) + 2 * sizeof(VT));
+  int64_t* sh_rp = reinterpret_cast<int64_t*>(fill_sh + 2 * win_bytes);
+  int32_t* sh_cur = reinterpret_cast<int32_t*>(fill_sh + 2 * win_bytes + kFillRpBytes);
+  const size_t cur_bytes = SMEM ? (((size_t)n_cols * sizeof(int32_t) + 15) & ~(size_t)15) : 0;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(fill_sh + 2 * win_bytes + kFillRpBytes + cur_bytes);
+  auto wcol = [&](int j) { return reinterpret_cast<int32_t*>(fill_sh + j * win_bytes); };
+  auto wD = [&](int j) { return reinterpret_cast<VT*>(fill_sh + j * win_bytes + sizeof(int32_t) * (size_t)W); };
+  auto wL = [&](int j) {
+    return reinterpret_cast<VT*>(fill_sh + j * win_bytes + (sizeof(int32_t) + sizeof(VT)) * (size_t)W);
+  };
   int32_t* cur = cursor + (int64_t)b * n_cols;
   if (SMEM) {  // the block's cursors stay in shared memory for the whole pass
     for (int j = threadIdx.x; j < n_cols; j += blockDim.x) sh_cur[j] = cur[j];
-    __syncthreads();
     cur = sh_cur;
   }
-  for (int64_t r = blk_row[b]; r < blk_row[b + 1]; ++r) {
-    const int64_t s = rp[r], e = rp[r + 1];
-    for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) {
-      const int c = col[p];
-      const int32_t pos = cur[c];
-      cur[c] = pos + 1;
-      row_out[pos] = (int32_t)r;
-      DT[pos] = Dv[p];
-      LT[pos] = Lv[p];
-    }
-    __syncthreads();
+  // window k = elements [EA + k W, min(EA + (k + 1) W, EZ)); the arrays are
+  // zero padded past nnz to a multiple of 256 elements, so EZ is in bounds
+  const int64_t EA = rp[r0] & ~(kFillAlign - 1);
+  const int64_t EZ = (rp[r1] + kFillAlign - 1) & ~(kFillAlign - 1);
+  const int64_t n_win = (EZ - EA + W - 1) / W;
+  auto issue = [&](int64_t k) {  // thread 0: window k into buffer k & 1
+    const int j = (int)(k & 1);
+    const int64_t ws = EA + k * W;
+    const uint32_t n = (uint32_t)(EZ - ws < W ? EZ - ws : W);
+    mbar_expect_tx(&bar[j], n * (uint32_t)(sizeof(int32_t) + 2 * sizeof(VT)));
+    bulk_g2s(wcol(j), col + ws, n * (uint32_t)sizeof(int32_t), &bar[j]);
+    bulk_g2s(wD(j), Dv + ws, n * (uint32_t)sizeof(VT), &bar[j]);
+    bulk_g2s(wL(j), Lv + ws, n * (uint32_t)sizeof(VT), &bar[j]);
+  };
+  // window k's phase on its buffer is the (k >> 1)-th; the outcome is made uniform over the block
+  auto wait_win = [&](int64_t k) -> bool {
+    const bool ok = mbar_wait(&bar[k & 1], (uint32_t)((k >> 1) & 1), kMbarSpins);
+    return __syncthreads_and(ok) != 0;
+  };
+  auto land = [&](int64_t k) {  // let windows k and k + 1 (issued ones) arrive
+    if (k < n_win) mbar_wait(&bar[k & 1], (uint32_t)((k >> 1) & 1), kMbarSpins);
+    if (k + 1 < n_win) mbar_wait(&bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), kMbarSpins);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (n_win > 1) issue(1);
+  }
+  int64_t k = 0;
+  if (!wait_win(0)) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    land(0);
+    return;
+  }
+  int64_t ws = EA, we = EA + W < EZ ? EA + W : EZ;
+  for (int64_t c0 = r0; c0 < r1; c0 += kFillRows) {
+    const int nr = (int)(r1 - c0 < kFillRows ? r1 - c0 : kFillRows);
+    __syncthreads();  // the previous chunk is done with sh_rp
+    for (int i = threadIdx.x; i <= nr; i += blockDim.x) sh_rp[i] = rp[c0 + i];
+    __syncthreads();
+    for (int i = 0; i < nr; ++i) {
+      int64_t sp = sh_rp[i];
+      const int64_t ep = sh_rp[i + 1];
+      const int32_t r = (int32_t)(c0 + i);
+      while (true) {
+        const int64_t hi = ep < we ? ep : we;
+        const int j = (int)(k & 1);
+        const int32_t* cc = wcol(j);
+        const VT* dd = wD(j);
+        const VT* ll = wL(j);
+        for (int64_t p = sp + threadIdx.x; p < hi; p += kFillThreads) {
+          const int o = (int)(p - ws);
+          const int c = cc[o];
+          const int32_t pos = cur[c];
+          cur[c] = pos + 1;
+          row_out[pos] = r;
+          DT[pos] = dd[o];
+          LT[pos] = ll[o];
+        }
+        if (ep <= we) break;
+        // the row continues in window k + 1: free buffer k & 1 for window k + 2
+        __syncthreads();
+        if (threadIdx.x == 0 && k + 2 < n_win) issue(k + 2);
+        ++k;
+        if (!wait_win(k)) {
+          if (threadIdx.x == 0) atomicOr(err, 1);
+          land(k);
+          return;
+        }
+        ws += W;
+        we = ws + W < EZ ? ws + W : EZ;
+        sp = hi;
+      }
+      __syncthreads();  // the row's cursor updates are done
+    }
+  }
+  land(k + 1);  // nothing is normally in flight here; never leave with a copy pending
 }
 
 template <typename VT>
@@ -1191,9 +1301,17 @@ void launch_moments(int fmt, const int64_t* rp, int64_t n_rows, const void* Dv, 
                                          ll, dl);
 }
 
+constexpr size_t kCscSmemMax = 200 * 1024;  // per-block column table kept in shared memory
+
 void launch_csc_count(const int64_t* rp, const int32_t* col, const int64_t* blk_row, int n_blk,
                       int32_t n_cols, int32_t* cnt, cudaStream_t s) {
-  k_csc_count<<<n_blk, 256, 0, s>>>(rp, col, blk_row, n_cols, cnt);
+  const size_t smem = (size_t)n_cols * sizeof(int32_t);
+  if (smem <= kCscSmemMax) {
+    cudaFuncSetAttribute(k_csc_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_csc_count<true><<<n_blk, 1024, smem, s>>>(rp, col, blk_row, n_cols, cnt);
+  } else {
+    k_csc_count<false><<<n_blk, 1024, 0, s>>>(rp, col, blk_row, n_cols, cnt);
+  }
 }
 
 void launch_csc_colsum(const int32_t* cnt, int n_blk, int32_t n_cols, int64_t* tot, cudaStream_t s) {
@@ -1204,35 +1322,46 @@ void launch_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int64_t* 
   k_csc_offsets<<<(n_cols + 255) / 256, 256, 0, s>>>(cnt, n_blk, n_cols, cp);
 }
 
-constexpr size_t kCscFillSmemMax = 200 * 1024;
-
-void launch_csc_fill(int fmt, const int64_t* rp, const int32_t* col, const void* Dv, const void* Lv,
-                     const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor,
-                     int32_t* row_out, void* DT, void* LT, cudaStream_t s) {
-  // cursors in shared memory when one block's row of the table fits
-  const size_t smem = (size_t)n_cols * sizeof(int32_t);
-  const bool use_smem = smem <= kCscFillSmemMax;
-  if (fmt == 0) {
-    if (use_smem) {
-      cudaFuncSetAttribute(k_csc_fill<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_csc_fill<float, true><<<n_blk, 256, smem, s>>>(rp, col, (const float*)Dv, (const float*)Lv, blk_row,
-                                                       n_cols, cursor, row_out, (float*)DT, (float*)LT);
-    } else {
-      k_csc_fill<float, false><<<n_blk, 256, 0, s>>>(rp, col, (const float*)Dv, (const float*)Lv, blk_row,
-                                                     n_cols, cursor, row_out, (float*)DT, (float*)LT);
-    }
-  } else {
-    if (use_smem) {
-      cudaFuncSetAttribute(k_csc_fill<uint16_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_csc_fill<uint16_t, true><<<n_blk, 256, smem, s>>>(rp, col, (const uint16_t*)Dv, (const uint16_t*)Lv,
-                                                          blk_row, n_cols, cursor, row_out, (uint16_t*)DT,
-                                                          (uint16_t*)LT);
-    } else {
-      k_csc_fill<uint16_t, false><<<n_blk, 256, 0, s>>>(rp, col, (const uint16_t*)Dv, (const uint16_t*)Lv,
-                                                        blk_row, n_cols, cursor, row_out, (uint16_t*)DT,
-                                                        (uint16_t*)LT);
-    }
+// Window length W (a multiple of kFillAlign, at most 8192) from the shared
+// memory left after the row-pointer chunk and, when they fit with W >= 1024,
+// the block's cursors.
+template <typename VT>
+static void fill_inst(const Geometry& g, const int64_t* rp, const int32_t* col, const void* Dv, const void* Lv,
+                      const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor, int32_t* row_out,
+                      void* DT, void* LT, int* err, cudaStream_t s) {
+  const size_t limit = g.smem_limit;
+  const size_t per_w = 2 * (sizeof(int32_t) + 2 * sizeof(VT));
+  auto w_for = [&](bool sc) -> int {
+    const size_t fixed = csc_fill_smem<VT>(0, n_cols, sc);
+    if (fixed >= limit) return 0;
+    const size_t w = std::min<size_t>((limit - fixed) / per_w, 8192) & ~(size_t)(kFillAlign - 1);
+    return (int)w;
+  };
+  bool sc = true;
+  int W = w_for(true);
+  if (W < 1024) {
+    sc = false;
+    W = w_for(false);
   }
+  const size_t smem = csc_fill_smem<VT>(W, n_cols, sc);
+  if (sc) {
+    cudaFuncSetAttribute(k_csc_fill<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_csc_fill<VT, true><<<n_blk, kFillThreads, smem, s>>>(rp, col, (const VT*)Dv, (const VT*)Lv, blk_row, n_cols,
+                                                            cursor, row_out, (VT*)DT, (VT*)LT, W, err);
+  } else {
+    cudaFuncSetAttribute(k_csc_fill<VT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_csc_fill<VT, false><<<n_blk, kFillThreads, smem, s>>>(rp, col, (const VT*)Dv, (const VT*)Lv, blk_row, n_cols,
+                                                             cursor, row_out, (VT*)DT, (VT*)LT, W, err);
+  }
+}
+
+void launch_csc_fill(const Geometry& g, int fmt, const int64_t* rp, const int32_t* col, const void* Dv,
+                     const void* Lv, const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor,
+                     int32_t* row_out, void* DT, void* LT, int* err, cudaStream_t s) {
+  if (fmt == 0)
+    fill_inst<float>(g, rp, col, Dv, Lv, blk_row, n_blk, n_cols, cursor, row_out, DT, LT, err, s);
+  else
+    fill_inst<uint16_t>(g, rp, col, Dv, Lv, blk_row, n_blk, n_cols, cursor, row_out, DT, LT, err, s);
 }
 
 void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_t* row, const void* DT,

@@ -81,6 +81,63 @@ def test_csc_bit_exact(lib, tiny, rows):
     np.testing.assert_array_equal(gL.view(np.uint32), LT.view(np.uint32))
 
 
+def _csc_of_device_rows(rp, col, D, L, n_cols):
+    """The CSC copy the library must build: rows with nonzeros first, then
+    the rest (ALL-row mode), transposed stably.  Moving the empty rows back
+    keeps the nonzero stream in its order."""
+    lens = np.diff(rp)
+    lens = np.concatenate([lens[lens > 0], lens[lens == 0]])
+    rp2 = np.zeros(len(lens) + 1, np.int64)
+    rp2[1:] = np.cumsum(lens)
+    return oracle.transpose_csr(rp2, col, n_cols, D, L)
+
+
+@pytest.mark.parametrize("case", ["wide", "long_rows", "many_short_rows"])
+@pytest.mark.parametrize("fmt", ["fp32", "bf16"])
+def test_csc_bit_exact_shapes(lib, case, fmt):
+    """Shapes that take the transpose's other paths: column tables too large
+    for shared memory, rows longer than two bulk-copy windows, and blocks
+    with more rows than one staged row-pointer chunk."""
+    rng = np.random.default_rng(17)
+    if case == "wide":
+        rp, col, D, L = phantom.random_csr(300, 60000, 0.02, seed=1, empty_rows=20)
+    elif case == "long_rows":
+        n_cols, lens = 30000, [25000, 3, 29999, 0, 17000, 1]
+        cols = [np.sort(rng.choice(n_cols, k, replace=False)).astype(np.int32) for k in lens]
+        rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        col = np.concatenate(cols)
+        D = rng.uniform(0.1, 1.0, len(col)).astype(np.float32)
+        L = (D * rng.uniform(1.0, 9.0, len(col))).astype(np.float32)
+    else:
+        n = 400000
+        c1 = rng.integers(0, 32, n)
+        c2 = rng.integers(32, 64, n)
+        col = np.stack([c1, c2], 1).ravel().astype(np.int32)
+        rp = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+        D = rng.uniform(0.1, 1.0, 2 * n).astype(np.float32)
+        L = (D * rng.uniform(1.0, 9.0, 2 * n)).astype(np.float32)
+    n_cols = int(col.max()) + 1 if len(col) else 1
+    n_cols = max(n_cols, 60000 if case == "wide" else n_cols)
+    mask = np.ones(len(rp) - 1, np.uint32)
+    with lib.Handle(0) as h:
+        h.load_influence(rp, col, D, L, mask, n_cols, fmt=fmt)
+        gcp, grow, gD, gL = h.get_csc()
+        if fmt != "fp32":
+            vox, _ = h.get_rows()
+    if fmt == "fp32":
+        cp, row, DT, LT = _csc_of_device_rows(rp, col, D, L, n_cols)
+        np.testing.assert_array_equal(gcp, cp)
+        np.testing.assert_array_equal(grow, row)
+        np.testing.assert_array_equal(gD.view(np.uint32), DT.view(np.uint32))
+        np.testing.assert_array_equal(gL.view(np.uint32), LT.view(np.uint32))
+    else:
+        # pattern and row order bit-exact; values are the dequantised stored values
+        cp, row, DT, LT = _csc_of_device_rows(rp, col, D, L, n_cols)
+        np.testing.assert_array_equal(gcp, cp)
+        np.testing.assert_array_equal(grow, row)
+        assert np.all(np.abs(gD - DT) <= 2.0 ** -8 * np.abs(DT) * 1.0001)
+
+
 def test_moments_fp64(lib, tiny):
     pl, P, R = tiny
     with handle(lib, pl, rows="roi") as h:
