@@ -232,7 +232,7 @@ def run_gpu_arm(args):
     roi = timed_run("roi") if args.roi else None
     prec = {}
     if args.precision:
-        # FP64 reference outputs: the FP64-accumulated final pass of an FP32
+        # FP64-class reference outputs: the double-float final pass of an FP32
         # handle (the FP32 inputs multiplied in FP64)
         ref = Handle(local, stream=stream)
         ref.load_plan(plan)

@@ -191,7 +191,8 @@ int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
 int fredopt_iterate(fredopt_t h, int iters);
 
 /* Finish: w_out float[n_spots]; dose_out, letd_out float[n_vox] in voxel
- * order (LETd = Lw/Dw, 0 where Dw = 0; Eq. 1) from an FP64-accumulated final
+ * order (LETd = Lw/Dw, 0 where Dw = 0; Eq. 1) from a double-float (about 48-bit,
+ * exact products) accumulated final
  * product; the FP64 feasibility and objective check goes to `rep`.  Any
  * output pointer may be NULL. */
 int fredopt_end(fredopt_t h, float* w_out, float* dose_out, float* letd_out, fredopt_report* rep,
@@ -253,7 +254,8 @@ int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_ou
  * PTV rule "98% of the volume receives at least 95% of the prescription") ----
  *
  * The voxel values are those of fredopt_end's final pass: (D w)_i and
- * (L w)_i accumulated in FP64 over the stored values, then rounded once to
+ * (L w)_i accumulated in double-float (about 48 bits; exact products, relative
+ * error per addition <= 3 * 2^-48) over the stored values, then rounded once to
  * FP32 as dose = (D w)_i, LETd = (L w)_i / (D w)_i (0 where (D w)_i <= 0),
  * cDL = c_cdl (L w)_i, with c_cdl of the last begin (default 0.04 um/keV).
  * A structure is the set of voxels whose mask has bit struct_bit set.

@@ -1216,7 +1216,7 @@ int fredopt_end(fredopt_t h, float* w_out, float* dose_out, float* letd_out, fre
     if (cudaEventElapsedTime(&ms, h->ev_it0, h->ev_it1) == cudaSuccess) h->device_ms += ms;
     h->it_pending = false;
   }
-  // final FP64-accumulated product over every row
+  // final double-float-accumulated product over every row
   CK(h->y64.ensure(std::max<int64_t>(1, h->V)));
   float* dptr = nullptr;
   float* lptr = nullptr;

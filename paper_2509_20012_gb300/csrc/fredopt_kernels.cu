@@ -155,6 +155,54 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// ---- double-float (double-word) accumulation ----
+// A value hi + lo held in two FP32 numbers (|lo| <= ulp(hi) / 2): about 48
+// significant bits at FP32 speed.  GB300's FP64 rate is a small fraction of
+// its FP32 rate, so the final FP64-class pass accumulates in this form.
+// Products are exact (TwoProd with an FMA); additions use the accurate
+// double-word sum of Joldes, Muller and Popescu (ACM TOMS 44(2), 2017,
+// relative error <= 3 * 2^-48), built from Knuth's TwoSum and Dekker's
+// FastTwoSum.  Every operation is an explicitly rounded intrinsic, so the
+// compiler cannot fuse or reorder any step.
+struct DF {
+  float hi, lo;
+  __device__ DF() : hi(0.0f), lo(0.0f) {}
+  __device__ explicit DF(float v) : hi(v), lo(0.0f) {}
+  __device__ DF(float h, float l) : hi(h), lo(l) {}
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return DF(s, e);
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = two_sum(x.hi, y.hi);
+  const DF t = two_sum(x.lo, y.lo);
+  const DF v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+// c + a * b: the accumulation step of the streaming core for each accumulator type
+__device__ __forceinline__ float acc_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ DF acc_fma(float a, float b, DF c) {
+  const float p = __fmul_rn(a, b);
+  return df_add(c, DF(p, __fmaf_rn(a, b, -p)));  // a * b = p + (a * b - p) exactly
+}
+template <>
+__device__ __forceinline__ DF warp_sum(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const DF w(__shfl_xor_sync(kFull, v.hi, o), __shfl_xor_sync(kFull, v.lo, o));
+    v = df_add(v, w);
+  }
+  return v;
+}
+
 // ---- mbarrier + bulk copy (TMA engine, non-tensor form) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -259,7 +307,7 @@ __device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
   int row = 0, base = 0;  // relative to r0
   int ends = (lane < nrows) ? (int)(ptr[r0 + 1 + lane] - start) : pe;
   int e_cur = __shfl_sync(kFull, ends, 0);
-  Acc sA = 0, sB = 0, myA = 0, myB = 0;
+  Acc sA{}, sB{}, myA{}, myB{};
   bool done = false;
 
   // consume the U blocks of one unit starting at offset b
@@ -284,18 +332,18 @@ __device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
         for (int q = 0; q < V; ++q) {
           const int e = e0 + q;
           if (e >= lo && e < hi) {
-            if (USE_A) sA = fma((Acc)av[q], (Acc)gv[q].x, sA);
-            sB = fma((Acc)bv[q], (Acc)gv[q].y, sB);
+            if (USE_A) sA = acc_fma(av[q], gv[q].x, sA);
+            sB = acc_fma(bv[q], gv[q].y, sB);
           }
         }
         if (e_cur > bb + BLK) break;  // the open segment continues in the next block
         const Acc tA = warp_sum(sA), tB = warp_sum(sB);
-        sA = 0; sB = 0;
+        sA = Acc{}; sB = Acc{};
         if (lane == row - base) { myA = tA; myB = tB; }
         ++row;
         if (row - base == 32 || row == nrows) {
           flush(r0 + base, row - base, myA, myB);
-          myA = 0; myB = 0;
+          myA = Acc{}; myB = Acc{};
           if (row == nrows) { done = true; return; }
           base = row;
           ends = (base + lane < nrows) ? (int)(ptr[r0 + base + 1 + lane] - start) : pe;
@@ -377,7 +425,7 @@ __device__ __forceinline__ void row_objective(const Tables& t, uint32_t m, doubl
 template <typename VT, int EPI, bool XS, bool S>
 __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(FwdArgs a, Tables t) {
   extern __shared__ __align__(128) unsigned char smem[];
-  using Acc = typename std::conditional<EPI == EPI_FINAL, double, float>::type;
+  using Acc = typename std::conditional<EPI == EPI_FINAL, DF, float>::type;
   const float* __restrict__ x = a.x;
   if (XS) {
     float* xs = reinterpret_cast<float*>(smem);

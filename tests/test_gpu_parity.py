@@ -483,9 +483,10 @@ def test_launch_count_and_timing(lib, tiny):
 
 
 def test_final_pass_is_fp64_product_of_fp32_inputs(lib, tiny):
-    """With FP32 storage the final pass (FP64 accumulation) equals the FP64
-    oracle product to FP64 rounding; bench.py uses it as the FP64 reference
-    of the 16-bit storage errors."""
+    """With FP32 storage the final pass (double-float accumulation: exact
+    products, <= 3 * 2^-48 relative error per addition) equals the FP64
+    oracle product up to the FP32 rounding of its outputs; bench.py uses it
+    as the FP64-class reference of the 16-bit storage errors."""
     pl, P, R = tiny
     rng = np.random.default_rng(9)
     w = rng.uniform(0.0, 2.0, pl.n_spots).astype(np.float32)
