@@ -108,7 +108,10 @@ typedef struct fredopt_params {
   int32_t sweep_blocks;   /* 0 (default): simultaneous feasibility step (Cimmino).  M in
                              1..FREDOPT_MAX_SWEEP_BLOCKS: block-iterative sweep of Fig. 2 over M
                              voxel blocks (see fredopt_sweep_step) */
-  int32_t reserved;       /* 0 */
+  int32_t tile_balance;   /* 1 (default): the forward product's warps claim row tiles of
+                             decreasing size from a counter, so SMs that stream faster take
+                             more of them (the SMs of a GB300 differ by up to ~13% in streaming
+                             rate); 0: one static tile per warp.  Results do not change. */
 } fredopt_params;
 
 #define FREDOPT_MAX_SWEEP_BLOCKS 1024

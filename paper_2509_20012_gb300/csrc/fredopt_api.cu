@@ -82,6 +82,9 @@ struct fredopt_ctx {
   DBuf<int32_t> crow;
   DBuf<uint8_t> DTv, LTv;
   DBuf<int64_t> warp_row_hot, warp_row_all, chunk_ptr;
+  DBuf<int64_t> tile_row_hot;  // claimed tiles of the streamed rows (guided sizes)
+  int n_tiles_hot = 0;
+  DBuf<unsigned int> fsched;   // counters of the claimed tiles
   DBuf<int32_t> col_chunk, warp_chunk;
   int64_t n_chunks = 0;
   bool hint_fwd = true, hint_bwd = true;
@@ -118,7 +121,7 @@ struct fredopt_ctx {
   DBuf<DevState> st;
   DBuf<LogEntry> log;
   DBuf<int> errw;
-  size_t off_f = 0, off_bc = 0, off_g = 0, off_k2 = 0, off_fin = 0, off_cnt = 0, n_part = 0;
+  size_t off_f = 0, off_bc = 0, off_g = 0, off_k2 = 0, off_fin = 0, off_cnt = 0, off_stage = 0, n_part = 0;
 
   // solve
   bool begun = false;
@@ -336,11 +339,15 @@ FwdArgs fwd_args(fredopt_t h, bool hot) {
   a.sD = h->fmt ? h->sD.p : nullptr;
   a.sL = h->fmt ? h->sL.p : nullptr;
   a.warp_row = hot ? h->warp_row_hot.p : h->warp_row_all.p;
+  if (hot && h->prm.tile_balance && h->n_tiles_hot > 0) {
+    a.warp_row = h->tile_row_hot.p;
+    a.sched = h->fsched.p;
+  }
   a.n_x = h->n;
   a.n_x_pad = h->n_pad;
   a.mask = h->mask.p;
   a.n_hot = h->n_hot;
-  a.n_warps = h->geo.fwd_warps;
+  a.n_warps = a.sched ? h->n_tiles_hot : h->geo.fwd_warps;
   a.st = h->st.p;
   a.voxel = h->perm ? h->voxel.p : nullptr;
   return a;
@@ -449,6 +456,7 @@ void enqueue_sweep(fredopt_t h, const float* w, int use_coef, double lam, double
     FwdArgs fa = fwd_args(h, true);
     fa.warp_row = h->sweep_wr.p + 2 * h->sweep_wr_off[t];
     fa.n_warps = h->sweep_warps[t];
+    fa.sched = nullptr;  // the block's own static tiles
     fa.x = h->xs.p;
     fa.y = h->ys.p;
     run(h, 0, [&] { launch_forward(G, h->fmt, EPI_STORE, h->hint_fwd, fa, h->tab, s); });
@@ -501,7 +509,7 @@ void enqueue_iteration(fredopt_t h) {
     fa.part = part_f;
     run(h, 0, [&] { launch_forward(G, h->fmt, EPI_OBJ, h->hint_fwd, fa, t, s); });
     for (int step = 0; step < N; ++step) {
-      int nf = G.fwd_warps;
+      int nf = fa.n_warps;
       if (step > 0) {
         run(h, 5, [&] { launch_apply_step(h->n_hot, h->n, h->w.p, h->g.p, h->yw.p, h->yg.p, h->st.p, s); });
         run(h, 5, [&] {
@@ -522,7 +530,10 @@ void enqueue_iteration(fredopt_t h) {
       fb.r_out = nullptr;
       fb.part = part_bc;
       run(h, 0, [&] { launch_forward(G, h->fmt, EPI_BC, h->hint_fwd, fb, t, s); });
-      run(h, 4, [&] { launch_finish(step, part_f, nf, part_bc, G.fwd_warps, part_g, G.col_blocks, h->st.p, s); });
+      run(h, 4, [&] {
+        launch_finish(step, part_f, nf, part_bc, fa.n_warps, part_g, G.col_blocks, h->st.p,
+                      h->part.p + h->off_stage, s);
+      });
     }
   } else {
     run(h, 0, [&] { launch_forward(G, h->fmt, EPI_STORE, h->hint_fwd, fa, t, s); });
@@ -550,6 +561,47 @@ void enqueue_iteration(fredopt_t h) {
   run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
 }
 
+// Tiles for warps that claim them in order (guided self-scheduling): the
+// first W tiles each hold half of a warp's share of rows [0, n) (cost:
+// nonzeros + row_cost per row), the next W a quarter, then an eighth, a
+// sixteenth, a thirty-second, and 2W tiles of a sixty-fourth, so the last
+// tiles to be claimed are short and the warps finish close together.
+// Always kGuidedTilesPerWarp * W tiles (some may be empty), so the tile
+// count, which kernels and captured graphs hold by value, does not depend on
+// row_cost.  Returns 2 * count row bounds.
+constexpr int kGuidedTilesPerWarp = 7;
+std::vector<int64_t> guided_tiles(const std::vector<int64_t>& rp, int64_t n, int W, int64_t row_cost) {
+  const int count = kGuidedTilesPerWarp * W;
+  std::vector<int64_t> out(2 * (size_t)count, n > 0 ? n : 0);
+  if (n <= 0 || W <= 0) return out;
+  auto prefix = [&](int64_t r) { return (double)(rp[r] - rp[0]) + (double)row_cost * (double)r; };
+  const double share = prefix(n) / W;
+  const std::pair<double, int> rounds[] = {{0.5, W}, {0.25, W}, {0.125, W}, {0.0625, W}, {0.03125, W},
+                                           {0.015625, 2 * W}};
+  double target = 0.0;
+  int64_t lo = 0;
+  int k = 0;
+  for (const auto& rd : rounds) {
+    for (int i = 0; i < rd.second; ++i, ++k) {
+      target += rd.first * share;
+      int64_t hi = n;
+      if (k + 1 < count) {
+        int64_t x = lo, y = n;  // first row m with prefix(m) >= target
+        while (x < y) {
+          const int64_t m = (x + y) / 2;
+          if (prefix(m) < target) x = m + 1;
+          else y = m;
+        }
+        hi = x;
+      }
+      out[2 * (size_t)k] = lo;
+      out[2 * (size_t)k + 1] = hi;
+      lo = hi;
+    }
+  }
+  return out;
+}
+
 // Warp partitions.  A segment's sum does not depend on which warp streams it
 // (lanes take elements by their absolute block-aligned position and add them
 // in order), so these weights change the speed, never a result bit.
@@ -559,7 +611,12 @@ int set_fwd_schedule(fredopt_t h, int64_t row_cost) {
       h->h_rp, {{0, h->n_hot_ne}, {h->n_hot, h->n_hot + h->n_cold_ne}}, h->geo.fwd_warps, row_cost);
   CK(cudaMemcpyAsync(h->warp_row_hot.p, wr.data(), wr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->warp_row_all.p, wa.data(), wa.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  const std::vector<int64_t> tl = guided_tiles(h->h_rp, h->n_hot_ne, h->geo.fwd_warps, row_cost);
+  if ((size_t)h->tile_row_hot.n < std::max<size_t>(2, tl.size())) CK(h->tile_row_hot.alloc(std::max<size_t>(2, tl.size())));
+  if (!tl.empty())
+    CK(cudaMemcpyAsync(h->tile_row_hot.p, tl.data(), tl.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  h->n_tiles_hot = (int)(tl.size() / 2);
   h->row_cost = row_cost;
   return FREDOPT_OK;
 }
@@ -606,6 +663,8 @@ int check_sticky(fredopt_t h) {
   if (err) {
     const int zero = 0;
     cudaMemcpy(&h->st.p->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    // a pass that gave up may have left its tile counters set
+    if (h->fsched.p) cudaMemset(h->fsched.p, 0, 2 * sizeof(unsigned int));
     return fail(h, FREDOPT_ERR_TIMEOUT, "a bounded device-side wait gave up (bulk copy)");
   }
   return FREDOPT_OK;
@@ -674,6 +733,7 @@ void fredopt_default_params(fredopt_params* p) {
   p->c_cdl = 0.04;
   p->log_capacity = 4096;
   p->use_graphs = 1;
+  p->tile_balance = 1;
 }
 
 const char* fredopt_strerror(int code) {
@@ -983,6 +1043,8 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   h->n_cold_ne = n_cold_ne;
   CK(h->warp_row_hot.alloc(2 * (size_t)h->geo.fwd_warps));
   CK(h->warp_row_all.alloc(2 * (size_t)h->geo.fwd_warps));
+  CK(h->fsched.ensure(2));
+  CK(cudaMemsetAsync(h->fsched.p, 0, 2 * sizeof(unsigned int), s));
   rc = set_fwd_schedule(h, FO_ROW_COST);
   if (rc) return rc;
   // streaming (evict-first) loads when the streamed matrices do not fit in L2
@@ -1006,13 +1068,16 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   CK(cudaMemsetAsync(h->r.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
   CK(h->chunk_sum.alloc(h->n_chunks));
   const Geometry& G = h->geo;
+  // forward partials: one per tile (at most 7 guided tiles per warp)
+  const int max_tiles = kGuidedTilesPerWarp * G.fwd_warps;
   h->off_f = 0;
-  h->off_bc = h->off_f + std::max(G.fwd_warps, G.row_blocks);
-  h->off_g = h->off_bc + 2 * G.fwd_warps;
+  h->off_bc = h->off_f + std::max(max_tiles, G.row_blocks);
+  h->off_g = h->off_bc + 2 * max_tiles;
   h->off_k2 = h->off_g + G.col_blocks;
   h->off_fin = h->off_k2 + 4 * G.row_blocks;
   h->off_cnt = h->off_fin + 8 * G.row_blocks;
-  h->n_part = h->off_cnt + 3 * G.row_blocks;
+  h->off_stage = h->off_cnt + 3 * G.row_blocks;
+  h->n_part = h->off_stage + 4 * kFinishBlocks;
   CK(h->part.alloc(h->n_part));
   CK(cudaMemsetAsync(h->part.p, 0, h->n_part * sizeof(double), s));
   h->y64.release(); h->yall.release(); h->fout_a.release(); h->fout_b.release();
@@ -1504,7 +1569,7 @@ int fredopt_objective(fredopt_t h, const float* x, double* f_out, float* grad_ou
   ca.part = h->part.p + h->off_g;
   run(h, 3, [&] { launch_colfinish(G, COL_GRAD, ca, s); });
   CK(cudaGetLastError());
-  std::vector<double> hp(G.fwd_warps);
+  std::vector<double> hp(fa.n_warps);
   CK(cudaMemcpyAsync(hp.data(), part_f, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (grad_out) CK(copy_out(h, grad_out, h->gtmp.p, (size_t)h->n * sizeof(float), flags));
   rc = check_sticky(h);

@@ -61,6 +61,8 @@ struct DevState {
   unsigned int done;  // last-block counter of the column finish
   int pad;
   double sweep_nv, sweep_mx;  // block-iterative sweep: violated rows and largest violation
+  unsigned int done_fin;      // last-block counter of the scalar finish
+  int pad2;
 };
 
 struct LogEntry {
@@ -81,7 +83,8 @@ struct FwdArgs {
   const void* Lv;
   const float* sD;       // row scales (16-bit storage) or null
   const float* sL;
-  const int64_t* warp_row;  // [2 * n_warps]: row range [r0, r1) of each warp (nonempty rows)
+  const int64_t* warp_row;  // [2 * n_warps]: row range [r0, r1) of each tile (nonempty rows)
+  unsigned int* sched;      // null: warp w streams tile w; else [2] counters of claimed tiles
   const float* x;
   int32_t n_x;           // number of spots
   int32_t n_x_pad;       // padded to a multiple of 4 (bulk-copy size)
@@ -90,8 +93,8 @@ struct FwdArgs {
   int64_t n_hot;
   float2* r_out;         // EPI_OBJ: objective residual, scaled for the CSC
   const float2* r_in;    // EPI_BC: residual of EPI_OBJ
-  double* part;          // per-warp partials, stride n_warps: [f] or [B', C']
-  int32_t n_warps;
+  double* part;          // per-tile partials, stride n_warps (the tile count): [f] or [B', C']
+  int32_t n_warps;        // number of tiles in warp_row (the partials' stride)
   DevState* st;
   // EPI_FINAL
   double2* y64;
@@ -177,8 +180,9 @@ void launch_backward(const Geometry& g, int fmt, bool stream_hint, bool use_D, c
 void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_t s);
 // grid 0: g.row_blocks CTAs (the partials' stride); otherwise that many
 void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s, int grid = 0);
+constexpr int kFinishBlocks = 64;  // CTAs of the scalar finish; stage holds 4 * kFinishBlocks doubles
 void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
-                   const double* part_g, int ng, DevState* st, cudaStream_t s);
+                   const double* part_g, int ng, DevState* st, double* stage, cudaStream_t s);
 void launch_count_rows(const Geometry& g, const Tables& t, const uint32_t* mask, const double* dd,
                        const double* ll, const double* dl, int64_t n_hot, double* part,
                        cudaStream_t s);

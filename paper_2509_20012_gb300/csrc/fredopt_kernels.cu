@@ -449,8 +449,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(Fwd
   }
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= a.n_warps) return;
-  const int64_t r0 = a.warp_row[2 * warp], r1 = a.warp_row[2 * warp + 1];
+  // Tiles: a warp streams tile `warp` (static schedule) or claims tiles in
+  // order from a counter (a.sched[0]) until none is left, so that faster SMs
+  // stream more of them; a.sched[1] counts the warps that are done and the
+  // last one resets both counters for the next launch.  A tile's sums do not
+  // depend on which warp streams it.
+  auto claim = [&]() -> int {
+    unsigned j = 0;
+    if (lane == 0) j = atomicAdd(&a.sched[0], 1u);
+    return (int)__shfl_sync(kFull, j, 0);
+  };
+  int job = a.sched ? claim() : warp;
   const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
   const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
   double acc0 = 0.0, acc1 = 0.0;  // per-lane partials of the epilogue reductions
@@ -492,17 +501,33 @@ __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(Fwd
       }
     }
   };
-  stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : kFwdUnroll16)>(a.col, Dv, Lv, a.rp, r0, r1, lane,
-                                                                          gather, flush);
-  if (EPI == EPI_OBJ || EPI == EPI_BC) {
-    acc0 = warp_sum(acc0);
-    acc1 = warp_sum(acc1);
-    if (lane == 0) {
-      a.part[warp] = acc0;
-      if (EPI == EPI_BC) a.part[a.n_warps + warp] = acc1;
+  while (job < a.n_warps) {
+    const int64_t r0 = a.warp_row[2 * job], r1 = a.warp_row[2 * job + 1];
+    acc0 = 0.0;
+    acc1 = 0.0;
+    stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : kFwdUnroll16)>(a.col, Dv, Lv, a.rp, r0, r1,
+                                                                            lane, gather, flush);
+    if (EPI == EPI_OBJ || EPI == EPI_BC) {  // partials per tile, summed later in tile order
+      const double s0 = warp_sum(acc0), s1 = warp_sum(acc1);
+      if (lane == 0) {
+        a.part[job] = s0;
+        if (EPI == EPI_BC) a.part[a.n_warps + job] = s1;
+      }
+    }
+    if (!a.sched) break;
+    job = claim();
+  }
+  if (a.sched && lane == 0) {
+    __threadfence();
+    const unsigned total = (gridDim.x * blockDim.x) >> 5;
+    if (atomicAdd(&a.sched[1], 1u) == total - 1) {
+      a.sched[0] = 0u;
+      a.sched[1] = 0u;
     }
   }
 }
+
+
 
 // ------------------------------------------------------------------ K3
 
@@ -711,15 +736,47 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
 
 // ------------------------------------------------------------------ K4
 
+// The partial sums (one per forward tile: tens of thousands) are added in
+// two fixed levels: every CTA sums one slice of each array, and the last CTA
+// to finish adds the slice sums in order and runs the trial loop.  FP64
+// additions are slow on a GB300 SM, so one CTA alone would take tens of us.
 __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, int nf,
                                                 const double* part_bc, int nbc, const double* part_g,
-                                                int ng, DevState* st) {
+                                                int ng, DevState* st, double* stage) {
   __shared__ double red[256];
-  const double f = block_sum_array(part_f, nf, red) + (step == 0 ? st->f_empty : 0.0);
-  const double Bp = block_sum_array(part_bc, nbc, red);
-  const double Cp = block_sum_array(part_bc + nbc, nbc, red);
-  const double gn2 = block_sum_array(part_g, ng, red);
+  __shared__ bool sh_last;
+  const int G = gridDim.x, b = blockIdx.x;
+  auto slice_sum = [&](const double* p, int n) {
+    const int per = (n + G - 1) / G;
+    const int i0 = min(n, b * per), i1 = min(n, i0 + per);
+    return block_sum_array(p + i0, i1 - i0, red);
+  };
+  const double f1 = slice_sum(part_f, nf);
+  const double b1 = slice_sum(part_bc, nbc);
+  const double c1 = slice_sum(part_bc + nbc, nbc);
+  const double g1 = slice_sum(part_g, ng);
+  if (threadIdx.x == 0) {
+    stage[b] = f1;
+    stage[G + b] = b1;
+    stage[2 * G + b] = c1;
+    stage[3 * G + b] = g1;
+    __threadfence();
+    sh_last = atomicAdd(&st->done_fin, 1u) == (unsigned)G - 1;
+  }
+  __syncthreads();
+  if (!sh_last) return;
+  __threadfence();
+  auto stage_sum = [&](int k) {  // written by other CTAs of this launch: read past L1
+    double v = 0.0;
+    for (int i = threadIdx.x; i < G; i += 256) v += __ldcg(&stage[k * G + i]);
+    return block_sum256(v, red);
+  };
+  const double f = stage_sum(0) + (step == 0 ? st->f_empty : 0.0);
+  const double Bp = stage_sum(1);
+  const double Cp = stage_sum(2);
+  const double gn2 = stage_sum(3);
   if (threadIdx.x != 0) return;
+  st->done_fin = 0u;
   if (step == 0) {
     st->f_start = f;
     st->accepted = 0;
@@ -1263,8 +1320,8 @@ void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cu
 }
 
 void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
-                   const double* part_g, int ng, DevState* st, cudaStream_t s) {
-  k_finish<<<1, 256, 0, s>>>(step, part_f, nf, part_bc, nbc, part_g, ng, st);
+                   const double* part_g, int ng, DevState* st, double* stage, cudaStream_t s) {
+  k_finish<<<kFinishBlocks, 256, 0, s>>>(step, part_f, nf, part_bc, nbc, part_g, ng, st, stage);
 }
 
 void launch_apply_step(int64_t n_hot, int n, float* w, const float* g, float2* yw, const float2* yg,

@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
                 ("reductions", ctypes.c_int32), ("max_trials", ctypes.c_int32),
                 ("cimmino_norm", ctypes.c_int32), ("grad_normalize", ctypes.c_int32),
                 ("c_cdl", ctypes.c_double), ("log_capacity", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("sweep_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("sweep_blocks", ctypes.c_int32), ("tile_balance", ctypes.c_int32)]
 
 
 class LogEntry(ctypes.Structure):

@@ -309,6 +309,29 @@ def test_deterministic_and_graph_equals_plain(lib, tiny):
     np.testing.assert_array_equal(w1, w3)
 
 
+@pytest.mark.parametrize("rows", ["all", "roi"])
+def test_claimed_tiles_equal_static_tiles(lib, tiny, rows):
+    """Warps claiming row tiles dynamically (the default) and one static tile
+    per warp give bit-identical iterates: a row's sums do not depend on the
+    warp that streams them.  The FP64 objective adds per-tile partials, so
+    the two tilings may group its sum differently (last-bit differences)."""
+    pl, P, R = tiny
+    w1, d1, l1, rep1, log1 = run_gpu(lib, pl, 12, rows=rows, tile_balance=1)
+    w0, d0, l0, rep0, log0 = run_gpu(lib, pl, 12, rows=rows, tile_balance=0)
+    np.testing.assert_array_equal(w1, w0)
+    np.testing.assert_array_equal(d1, d0)
+    for a, b in zip(log1, log0):
+        for k in a:
+            if k in ("f_start", "f_end"):
+                assert a[k] == pytest.approx(b[k], rel=1e-14, abs=0)
+            else:
+                assert a[k] == b[k], k
+    # each tiling on its own is deterministic, objective included
+    w2, *_, log2 = run_gpu(lib, pl, 12, rows=rows, tile_balance=1)
+    np.testing.assert_array_equal(w2, w1)
+    assert log2 == log1
+
+
 def test_checkpoint_resume_bit_exact(lib, tiny):
     pl, P, R = tiny
     with handle(lib, pl) as h:
