@@ -85,6 +85,9 @@ struct fredopt_ctx {
   DBuf<int64_t> tile_row_hot;  // claimed tiles of the streamed rows (guided sizes)
   int n_tiles_hot = 0;
   DBuf<unsigned int> fsched;   // counters of the claimed tiles
+  DBuf<int32_t> tile_chunk;    // claimed tiles of the transposed product: chunk bounds [n_tiles_bwd + 1]
+  int n_tiles_bwd = 0;
+  DBuf<unsigned int> bsched;
   DBuf<int32_t> col_chunk, warp_chunk;
   int64_t n_chunks = 0;
   bool hint_fwd = true, hint_bwd = true;
@@ -363,6 +366,11 @@ BwdArgs bwd_args(fredopt_t h, const float2* coef) {
   b.coef = coef;
   b.chunk_sum = h->chunk_sum.p;
   b.n_warps = h->geo.bwd_warps;
+  if (h->prm.tile_balance && h->n_tiles_bwd > 0) {
+    b.warp_chunk = h->tile_chunk.p;
+    b.n_warps = h->n_tiles_bwd;
+    b.sched = h->bsched.p;
+  }
   return b;
 }
 
@@ -625,7 +633,15 @@ int set_bwd_schedule(fredopt_t h, int64_t chunk_cost) {
   const std::vector<int64_t> w64 = partition_rows(h->h_cptr, h->n_chunks, h->geo.bwd_warps, chunk_cost);
   const std::vector<int32_t> w32(w64.begin(), w64.end());
   CK(cudaMemcpyAsync(h->warp_chunk.p, w32.data(), w32.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  // claimed tiles: guided sizes over the chunks (the same rule as the forward rows)
+  const std::vector<int64_t> tl = guided_tiles(h->h_cptr, h->n_chunks, h->geo.bwd_warps, chunk_cost);
+  std::vector<int32_t> tb(tl.size() / 2 + 1, 0);
+  for (size_t k = 0; k < tl.size() / 2; ++k) tb[k] = (int32_t)tl[2 * k];
+  tb.back() = tl.empty() ? 0 : (int32_t)tl.back();
+  if ((size_t)h->tile_chunk.n < tb.size()) CK(h->tile_chunk.alloc(tb.size()));
+  CK(cudaMemcpyAsync(h->tile_chunk.p, tb.data(), tb.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  h->n_tiles_bwd = (int)(tb.size() - 1);
   h->chunk_cost = chunk_cost;
   return FREDOPT_OK;
 }
@@ -665,6 +681,7 @@ int check_sticky(fredopt_t h) {
     cudaMemcpy(&h->st.p->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
     // a pass that gave up may have left its tile counters set
     if (h->fsched.p) cudaMemset(h->fsched.p, 0, 2 * sizeof(unsigned int));
+    if (h->bsched.p) cudaMemset(h->bsched.p, 0, 2 * sizeof(unsigned int));
     return fail(h, FREDOPT_ERR_TIMEOUT, "a bounded device-side wait gave up (bulk copy)");
   }
   return FREDOPT_OK;
@@ -1045,6 +1062,8 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   CK(h->warp_row_all.alloc(2 * (size_t)h->geo.fwd_warps));
   CK(h->fsched.ensure(2));
   CK(cudaMemsetAsync(h->fsched.p, 0, 2 * sizeof(unsigned int), s));
+  CK(h->bsched.ensure(2));
+  CK(cudaMemsetAsync(h->bsched.p, 0, 2 * sizeof(unsigned int), s));
   rc = set_fwd_schedule(h, FO_ROW_COST);
   if (rc) return rc;
   // streaming (evict-first) loads when the streamed matrices do not fit in L2

@@ -108,10 +108,11 @@ struct BwdArgs {
   const void* Dv;
   const void* Lv;
   const int64_t* chunk_ptr;   // [n_chunks + 1]
-  const int32_t* warp_chunk;  // [n_warps + 1]
+  const int32_t* warp_chunk;  // [n_warps + 1]: chunk range of each tile
+  unsigned int* sched;        // null: warp w streams tile w; else [2] counters of claimed tiles
   const float2* coef;         // per streamed row
   float* chunk_sum;
-  int32_t n_warps;
+  int32_t n_warps;            // number of tiles
 };
 
 struct ColArgs {

@@ -537,7 +537,6 @@ template <typename VT, bool S, bool UD>
 __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(BwdArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= a.n_warps) return;
   const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
   const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
   const float2* __restrict__ cf = a.coef;
@@ -546,8 +545,28 @@ __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(Bwd
   auto flush = [&](int64_t base, int cnt, float mA, float mB) {
     if (lane < cnt) out[base + lane] = UD ? mA + mB : mB;
   };
-  stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16)>(
-      a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[warp], a.warp_chunk[warp + 1], lane, gather, flush);
+  // tiles of column chunks, static (tile = warp) or claimed from a counter as
+  // in the forward product; a chunk's sum does not depend on its warp
+  auto claim = [&]() -> int {
+    unsigned j = 0;
+    if (lane == 0) j = atomicAdd(&a.sched[0], 1u);
+    return (int)__shfl_sync(kFull, j, 0);
+  };
+  int job = a.sched ? claim() : warp;
+  while (job < a.n_warps) {
+    stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16)>(
+        a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush);
+    if (!a.sched) break;
+    job = claim();
+  }
+  if (a.sched && lane == 0) {
+    __threadfence();
+    const unsigned total = (gridDim.x * blockDim.x) >> 5;
+    if (atomicAdd(&a.sched[1], 1u) == total - 1) {
+      a.sched[0] = 0u;
+      a.sched[1] = 0u;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ block reductions
