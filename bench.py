@@ -124,7 +124,7 @@ class ClockSampler:
 # two forward launches of an iteration); traffic grows with the nonzeros, so
 # it is scaled to the full plan.  FP32 storage only; the other storages have
 # no capture yet (null).
-FWD_TRAFFIC_PER_NNZ = {"fp32": 12.17}
+FWD_TRAFFIC_PER_NNZ = {"fp32": 12.48}
 
 
 def fwd_bytes(nnz, rows, vb, n_launch_obj, n_launch_bc):
