@@ -377,9 +377,14 @@ int fredopt_superiorize_batch(const fredopt_t* handles, int n, const float* cons
  * under `mem_cap_bytes` and fewer than `max_active` plans are loaded; each
  * admitted plan stays resident on its own stream and its iterations are
  * enqueued in rounds of `round_iters`, interleaved with the other active
- * plans, so that their kernels overlap on the device.  A plan's results do
- * not depend on its co-tenants (every tile shape depends on the plan alone):
- * they are bit-identical to a fredopt_superiorize call on the same inputs.
+ * plans, so that their kernels overlap on the device.  A plan admitted
+ * with no request waiting gets a CUDA stream priority below the plans
+ * already in flight (an older plan's kernels are scheduled first, younger
+ * plans fill the SMs it leaves idle), so it runs about as fast as alone;
+ * plans admitted from a backlog share the lowest priority and interleave.  A plan's results do not
+ * depend on its co-tenants (tiles depend on the plan alone and a tile's sums
+ * on nothing else): they are bit-identical to a fredopt_superiorize call on
+ * the same inputs.
  * All request pointers are host pointers owned by the caller and must stay
  * valid until the request is done (status DONE or an error).  Thread-safe. */
 typedef struct fredopt_request {

@@ -46,6 +46,8 @@ struct Req {
   cudaEvent_t round_done = nullptr;
   bool round_pending = false;
   fredopt_report rep{};
+  cudaStream_t stream = nullptr;  // the plan's stream, created with `prio`
+  int prio = 0;
 };
 
 }  // namespace
@@ -65,6 +67,7 @@ struct fredopt_server {
   std::vector<std::shared_ptr<Req>> active;
   int64_t mem_used = 0;
   int n_loading = 0;
+  int prio_least = 0, prio_greatest = 0;  // CUDA stream priority range (greatest is numerically lowest)
   int64_t next_id = 1;
   bool stop = false;
   std::thread loader, scheduler;
@@ -73,6 +76,14 @@ struct fredopt_server {
 };
 
 namespace {
+
+// Destroy a plan's handle and then its stream.
+void release(Req& q) {
+  if (q.h) fredopt_destroy(q.h);
+  q.h = nullptr;
+  if (q.stream) cudaStreamDestroy(q.stream);
+  q.stream = nullptr;
+}
 
 void set_error(fredopt_server* s, const std::shared_ptr<Req>& q, int code) {
   std::lock_guard<std::mutex> lk(s->mu);
@@ -102,10 +113,25 @@ void loader_main(fredopt_server* s) {
       s->n_loading += 1;
       q->status = LOADING;
       q->t_admit = s->now();
+      // Stream priority.  Admitted with no backlog (latency matters): the
+      // level below the youngest plan in flight, so the block scheduler
+      // serves older plans first and younger ones fill the SMs they leave
+      // idle.  Admitted while requests still wait (throughput matters): the
+      // lowest level, shared, so the plans interleave freely.
+      int lvl = s->prio_greatest;
+      for (const auto& kv : s->table) {
+        const Req& o = *kv.second;
+        if (&o != q.get() && (o.status == LOADING || o.status == RUNNING) && o.stream)
+          lvl = std::max(lvl, o.prio + 1);
+      }
+      q->prio = s->queue.empty() ? std::min(lvl, s->prio_least) : s->prio_least;
     }
     const fredopt_request& r = q->r;
     fredopt_t h = nullptr;
-    int rc = fredopt_create(&h, s->device, nullptr);
+    int rc = cudaStreamCreateWithPriority(&q->stream, cudaStreamNonBlocking, q->prio) == cudaSuccess
+                 ? FREDOPT_OK
+                 : FREDOPT_ERR_CUDA;
+    if (rc == FREDOPT_OK) rc = fredopt_create(&h, s->device, q->stream);
     if (rc == FREDOPT_OK)
       rc = fredopt_load_influence(h, r.n_vox, r.n_spots, r.nnz, r.row_ptr, r.col, r.D_val, r.L_val,
                                   r.voxel_mask, r.format, 0);
@@ -119,7 +145,8 @@ void loader_main(fredopt_server* s) {
       s->n_loading -= 1;
     }
     if (rc != FREDOPT_OK) {
-      if (h) fredopt_destroy(h);
+      q->h = h;
+      release(*q);
       set_error(s, q, rc);
       continue;
     }
@@ -139,10 +166,9 @@ void finish(fredopt_server* s, const std::shared_ptr<Req>& q) {
   const fredopt_request& r = q->r;
   fredopt_report rep{};
   int rc = fredopt_end(q->h, r.w_out, r.dose_out, r.letd_out, &rep, 0);
-  fredopt_destroy(q->h);
   cudaEventDestroy(q->round_done);
+  release(*q);
   std::lock_guard<std::mutex> lk(s->mu);
-  q->h = nullptr;
   q->rep = rep;
   q->status = rc == FREDOPT_OK ? DONE : rc;
   q->t_done = s->now();
@@ -174,9 +200,8 @@ void scheduler_main(fredopt_server* s) {
         if (rc == FREDOPT_OK && cudaEventRecord(q->round_done, fo::handle_stream(q->h)) != cudaSuccess)
           rc = FREDOPT_ERR_CUDA;
         if (rc != FREDOPT_OK) {
-          fredopt_destroy(q->h);
           cudaEventDestroy(q->round_done);
-          q->h = nullptr;
+          release(*q);
           {
             std::lock_guard<std::mutex> lk(s->mu);
             s->active.erase(std::remove(s->active.begin(), s->active.end(), q), s->active.end());
@@ -240,6 +265,16 @@ int fredopt_server_create(fredopt_server_t* out, int device, int64_t mem_cap_byt
   s->max_active = max_active;
   s->round_iters = round_iters;
   s->t0 = Clock::now();
+  {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(device);
+    if (cudaDeviceGetStreamPriorityRange(&s->prio_least, &s->prio_greatest) != cudaSuccess) {
+      cudaGetLastError();
+      s->prio_least = s->prio_greatest = 0;
+    }
+    cudaSetDevice(cur);
+  }
   s->loader = std::thread(loader_main, s);
   s->scheduler = std::thread(scheduler_main, s);
   *out = s;
