@@ -108,10 +108,12 @@ typedef struct fredopt_params {
   int32_t sweep_blocks;   /* 0 (default): simultaneous feasibility step (Cimmino).  M in
                              1..FREDOPT_MAX_SWEEP_BLOCKS: block-iterative sweep of Fig. 2 over M
                              voxel blocks (see fredopt_sweep_step) */
-  int32_t tile_balance;   /* 1 (default): the forward product's warps claim row tiles of
-                             decreasing size from a counter, so SMs that stream faster take
-                             more of them (the SMs of a GB300 differ by up to ~13% in streaming
-                             rate); 0: one static tile per warp.  Results do not change. */
+  int32_t tile_balance;   /* 1 (default): in passes of at least 16384 nonzeros per warp, the
+                             forward and transposed products' warps claim tiles of decreasing
+                             size from a counter, so SMs that stream faster take more of them
+                             (the SMs of a GB300 differ by up to ~13% in streaming rate);
+                             2: claim tiles in every pass; 0: one static tile per warp.
+                             Results do not change. */
 } fredopt_params;
 
 #define FREDOPT_MAX_SWEEP_BLOCKS 1024

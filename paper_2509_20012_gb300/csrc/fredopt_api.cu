@@ -333,6 +333,15 @@ void collect_timers(fredopt_t h) {
   h->timers_used = 0;
 }
 
+// Claimed tiles pay off when a pass is long enough for the SMs' different
+// streaming rates to matter; below kClaimMinNnzPerWarp nonzeros per warp the
+// claims cost more than they balance (tile_balance 2 claims always).
+constexpr int64_t kClaimMinNnzPerWarp = 16384;
+bool claim_tiles(fredopt_t h) {
+  if (h->prm.tile_balance == 2) return true;
+  return h->prm.tile_balance == 1 && h->nnz_hot >= kClaimMinNnzPerWarp * (int64_t)h->geo.fwd_warps;
+}
+
 FwdArgs fwd_args(fredopt_t h, bool hot) {
   FwdArgs a{};
   a.rp = h->rp.p;
@@ -342,7 +351,7 @@ FwdArgs fwd_args(fredopt_t h, bool hot) {
   a.sD = h->fmt ? h->sD.p : nullptr;
   a.sL = h->fmt ? h->sL.p : nullptr;
   a.warp_row = hot ? h->warp_row_hot.p : h->warp_row_all.p;
-  if (hot && h->prm.tile_balance && h->n_tiles_hot > 0) {
+  if (hot && claim_tiles(h) && h->n_tiles_hot > 0) {
     a.warp_row = h->tile_row_hot.p;
     a.sched = h->fsched.p;
   }
@@ -366,7 +375,7 @@ BwdArgs bwd_args(fredopt_t h, const float2* coef) {
   b.coef = coef;
   b.chunk_sum = h->chunk_sum.p;
   b.n_warps = h->geo.bwd_warps;
-  if (h->prm.tile_balance && h->n_tiles_bwd > 0) {
+  if (claim_tiles(h) && h->n_tiles_bwd > 0) {
     b.warp_chunk = h->tile_chunk.p;
     b.n_warps = h->n_tiles_bwd;
     b.sched = h->bsched.p;
@@ -1192,7 +1201,7 @@ int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
   if (p.reductions < 0 || p.max_trials < 1 || p.log_capacity < 0 ||
       (p.cimmino_norm != FREDOPT_NORM_ALL && p.cimmino_norm != FREDOPT_NORM_VIOLATED) ||
       !(p.c_cdl > 0.0) || !std::isfinite(p.beta0) || p.sweep_blocks < 0 ||
-      p.sweep_blocks > FREDOPT_MAX_SWEEP_BLOCKS)
+      p.sweep_blocks > FREDOPT_MAX_SWEEP_BLOCKS || p.tile_balance < 0 || p.tile_balance > 2)
     return fail(h, FREDOPT_ERR_INVALID_ARG, "bad parameters");
   DeviceGuard dg(h->device);
   cudaStream_t s = h->stream;

@@ -316,7 +316,7 @@ def test_claimed_tiles_equal_static_tiles(lib, tiny, rows):
     warp that streams them.  The FP64 objective adds per-tile partials, so
     the two tilings may group its sum differently (last-bit differences)."""
     pl, P, R = tiny
-    w1, d1, l1, rep1, log1 = run_gpu(lib, pl, 12, rows=rows, tile_balance=1)
+    w1, d1, l1, rep1, log1 = run_gpu(lib, pl, 12, rows=rows, tile_balance=2)
     w0, d0, l0, rep0, log0 = run_gpu(lib, pl, 12, rows=rows, tile_balance=0)
     np.testing.assert_array_equal(w1, w0)
     np.testing.assert_array_equal(d1, d0)
@@ -327,7 +327,7 @@ def test_claimed_tiles_equal_static_tiles(lib, tiny, rows):
             else:
                 assert a[k] == b[k], k
     # each tiling on its own is deterministic, objective included
-    w2, *_, log2 = run_gpu(lib, pl, 12, rows=rows, tile_balance=1)
+    w2, *_, log2 = run_gpu(lib, pl, 12, rows=rows, tile_balance=2)
     np.testing.assert_array_equal(w2, w1)
     assert log2 == log1
 
