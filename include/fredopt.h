@@ -342,10 +342,11 @@ int64_t fredopt_launch_count(fredopt_t h);
 /* ---- tile autotuning and batches of plans ----
  *
  * Tiles are the contiguous ranges of rows (forward product) and of column
- * chunks (transposed product) that each warp streams.  They are balanced by
- * nonzeros plus a weight per row end / per chunk.  A segment's sum does not
- * depend on which warp streams it, so the weights change speed, never a
- * result bit.  fredopt_autotune times the forward and transposed products
+ * chunks (transposed product) that warps stream: one per warp, or (see
+ * fredopt_params.tile_balance) 7 per warp of decreasing size, claimed in
+ * order.  Their sizes are measured in nonzeros plus a weight per row end /
+ * per chunk.  A segment's sum does not depend on which warp streams it, so
+ * the weights change speed, never a result bit.  fredopt_autotune times the forward and transposed products
  * with `reps` repetitions for each candidate weight (rows: 16..512, chunks:
  * 4..1024) and keeps the fastest pair; it may be called after load or after
  * begin.  fredopt_get_tuning reports the weights in use. */
