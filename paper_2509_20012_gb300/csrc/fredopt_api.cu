@@ -852,53 +852,15 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   cudaStream_t s = h->stream;
   join_in(h);
 
-  // ---- host copies of row_ptr and the mask; row_ptr checked on the host
-  std::vector<int64_t> rp0(n_vox + 1);
-  std::vector<uint32_t> m0(n_vox);
-  if (dev_ptr(flags)) {
-    CK(cudaMemcpyAsync(rp0.data(), row_ptr, (n_vox + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (n_vox) CK(cudaMemcpyAsync(m0.data(), voxel_mask, n_vox * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-  } else {
-    std::memcpy(rp0.data(), row_ptr, (n_vox + 1) * sizeof(int64_t));
-    if (n_vox) std::memcpy(m0.data(), voxel_mask, n_vox * sizeof(uint32_t));
-  }
-  if (rp0[0] != 0 || rp0[n_vox] != nnz) return fail(h, FREDOPT_ERR_PATTERN, "row_ptr[0] != 0 or row_ptr[n_vox] != nnz");
-  for (int64_t i = 0; i < n_vox; ++i)
-    if (rp0[i + 1] < rp0[i]) return fail(h, FREDOPT_ERR_PATTERN, "row_ptr not monotone");
-
-  // ---- device order of rows: streamed rows with nonzeros, streamed rows
-  // without, other rows with nonzeros, other rows without (each ascending)
-  std::vector<int64_t> order;
-  order.reserve(n_vox);
-  auto is_hot = [&](int64_t i) { return !roi || m0[i] != 0; };
-  auto has_nz = [&](int64_t i) { return rp0[i + 1] > rp0[i]; };
-  for (int64_t i = 0; i < n_vox; ++i) if (is_hot(i) && has_nz(i)) order.push_back(i);
-  const int64_t n_hot_ne = (int64_t)order.size();
-  for (int64_t i = 0; i < n_vox; ++i) if (is_hot(i) && !has_nz(i)) order.push_back(i);
-  const int64_t n_hot = (int64_t)order.size();
-  for (int64_t i = 0; i < n_vox; ++i) if (!is_hot(i) && has_nz(i)) order.push_back(i);
-  const int64_t n_cold_ne = (int64_t)order.size() - n_hot;
-  for (int64_t i = 0; i < n_vox; ++i) if (!is_hot(i) && !has_nz(i)) order.push_back(i);
-  bool perm = false;
-  for (int64_t r = 0; r < n_vox && !perm; ++r) perm = order[r] != r;
-  std::vector<int64_t> rp1;
-  if (perm) {
-    rp1.resize(n_vox + 1);
-    rp1[0] = 0;
-    for (int64_t r = 0; r < n_vox; ++r) rp1[r + 1] = rp1[r] + (rp0[order[r] + 1] - rp0[order[r]]);
-  }
-  const std::vector<int64_t>& rpd = perm ? rp1 : rp0;
   // every index / value array is zero padded past its last nonzero
   const int64_t nnz_alloc = ((nnz + 255) & ~255LL) + kPadElems;
 
-  // ---- upload + validate (on the input layout)
-  DBuf<int64_t> rp_in;
+  // ---- host inputs: their upload is issued first, so that the copy engine
+  // runs while the host checks row_ptr and orders the rows
   DBuf<int32_t> col_in;
   DBuf<float> D_in, L_in;
   const int32_t* colp = col;
   const float *Dp = D_val, *Lp = L_val;
-  CK(upload_vec(h, rp_in, rp0));
   if (!dev_ptr(flags)) {
     CK(col_in.alloc(nnz_alloc));
     CK(D_in.alloc(nnz_alloc));
@@ -915,6 +877,69 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     Dp = D_in.p;
     Lp = L_in.p;
   }
+
+  // ---- row_ptr and the mask on the host (read in place when they are host
+  // memory); row_ptr checked on the host
+  std::vector<int64_t> rp_copy;
+  std::vector<uint32_t> m_copy;
+  const int64_t* rp0 = row_ptr;
+  const uint32_t* m0 = voxel_mask;
+  if (dev_ptr(flags)) {
+    rp_copy.resize(n_vox + 1);
+    m_copy.resize(n_vox);
+    CK(cudaMemcpyAsync(rp_copy.data(), row_ptr, (n_vox + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (n_vox) CK(cudaMemcpyAsync(m_copy.data(), voxel_mask, n_vox * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rp0 = rp_copy.data();
+    m0 = m_copy.data();
+  }
+  if (rp0[0] != 0 || rp0[n_vox] != nnz) return fail(h, FREDOPT_ERR_PATTERN, "row_ptr[0] != 0 or row_ptr[n_vox] != nnz");
+  for (int64_t i = 0; i < n_vox; ++i)
+    if (rp0[i + 1] < rp0[i]) return fail(h, FREDOPT_ERR_PATTERN, "row_ptr not monotone");
+
+  // ---- device order of rows: streamed rows with nonzeros, streamed rows
+  // without, other rows with nonzeros, other rows without (each ascending);
+  // one pass over row_ptr and the mask assigns the groups
+  std::vector<uint8_t> grp(n_vox);
+  int64_t c0 = 0, c1 = 0, c2 = 0;  // counts in locals: no store-to-load chain between rows
+  for (int64_t i = 0; i < n_vox; ++i) {
+    const int g = ((!roi || m0[i] != 0) ? 0 : 2) + (rp0[i + 1] > rp0[i] ? 0 : 1);
+    grp[i] = (uint8_t)g;
+    c0 += g == 0;
+    c1 += g == 1;
+    c2 += g == 2;
+  }
+  const int64_t n_hot_ne = c0;
+  const int64_t n_hot = c0 + c1;
+  const int64_t n_cold_ne = c2;
+  std::vector<int64_t> order(n_vox);
+  bool perm = false;
+  {
+    int64_t p0 = 0, p1 = c0, p2 = c0 + c1, p3 = c0 + c1 + c2;
+    for (int64_t i = 0; i < n_vox; ++i) {
+      int64_t r;
+      switch (grp[i]) {
+        case 0: r = p0++; break;
+        case 1: r = p1++; break;
+        case 2: r = p2++; break;
+        default: r = p3++; break;
+      }
+      order[r] = i;
+      perm |= r != i;
+    }
+  }
+  std::vector<int64_t> rpd(n_vox + 1);
+  if (perm) {
+    rpd[0] = 0;
+    for (int64_t r = 0; r < n_vox; ++r) rpd[r + 1] = rpd[r] + (rp0[order[r] + 1] - rp0[order[r]]);
+  } else {
+    std::memcpy(rpd.data(), rp0, (n_vox + 1) * sizeof(int64_t));
+  }
+
+  // ---- validate (on the input layout)
+  DBuf<int64_t> rp_in;
+  CK(rp_in.alloc(n_vox + 1));
+  CK(cudaMemcpyAsync(rp_in.p, rp0, (n_vox + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
   launch_validate(rp_in.p, colp, Dp, Lp, n_vox, n_spots, nnz, h->errw.p, s);
   CK(cudaGetLastError());
@@ -1064,7 +1089,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
 #ifndef FO_ROW_COST
 #define FO_ROW_COST 64
 #endif
-  h->h_rp = rpd;
+  h->h_rp = std::move(rpd);
   h->n_hot_ne = n_hot_ne;
   h->n_cold_ne = n_cold_ne;
   CK(h->warp_row_hot.alloc(2 * (size_t)h->geo.fwd_warps));
