@@ -1001,6 +1001,10 @@ __global__ void k_quantize(int fmt, const int64_t* rp, int64_t n_rows, const flo
   }
 }
 
+// FP64-accurate row moments |D_i|^2, |L_i|^2, <D_i, L_i> of the stored
+// values in double-float (exact products, accurate double-word sums: relative
+// error <= 3 * 2^-48 per addition of these nonnegative terms), at FP32 speed;
+// the power-of-two row scales are applied at the end, exactly.
 template <typename VT>
 __global__ void k_moments(const int64_t* rp, int64_t n_rows, const VT* Dv, const VT* Lv,
                           const float* sD, const float* sL, double* dd, double* ll, double* dl) {
@@ -1008,19 +1012,22 @@ __global__ void k_moments(const int64_t* rp, int64_t n_rows, const VT* Dv, const
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += nw) {
     const int64_t s = rp[r], e = rp[r + 1];
-    const double sd = sD ? (double)sD[r] : 1.0, sl = sL ? (double)sL[r] : 1.0;
-    double a = 0.0, b = 0.0, c = 0.0;
+    DF a, b, c;
     for (int64_t p = s + lane; p < e; p += 32) {
-      const double d = sd * (double)to_f(Dv[p]);
-      const double l = sl * (double)to_f(Lv[p]);
-      a += d * d;
-      b += l * l;
-      c += d * l;
+      const float d = to_f(Dv[p]), l = to_f(Lv[p]);
+      a = acc_fma(d, d, a);
+      b = acc_fma(l, l, b);
+      c = acc_fma(d, l, c);
     }
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_sum(c);
-    if (lane == 0) { dd[r] = a; ll[r] = b; dl[r] = c; }
+    if (lane == 0) {
+      const double sd = sD ? (double)sD[r] : 1.0, sl = sL ? (double)sL[r] : 1.0;
+      dd[r] = (double)a * (sd * sd);
+      ll[r] = (double)b * (sl * sl);
+      dl[r] = (double)c * (sd * sl);
+    }
   }
 }
 
