@@ -460,7 +460,7 @@ def serving_benchmark(args, local, clinical=None):
 
 
 def batching_benchmark(args, local):
-    """SURVEY cfg3: (a) 16 independent plans, PTV 20-400 cc, nnz 6e5-7e7,
+    """Batching workloads: (a) 16 independent plans, PTV 20-400 cc, nnz 6e5-7e7,
     BF16, tiles autotuned per plan, run one after another vs as one batch
     graph per iteration; (b) 27 robustness scenarios stacked into one robust
     plan (one w meets the constraints in every scenario), BF16."""
@@ -705,7 +705,7 @@ def main():
         ws, rank, local = dist_env()
         torch.cuda.set_device(local)
         res = batching_benchmark(args, local)
-        print(json.dumps({"metric": "batching (SURVEY cfg3)", "n_gpus": 1, "data": "synthetic", **res}))
+        print(json.dumps({"metric": "batching", "n_gpus": 1, "data": "synthetic", **res}))
         return
     if args.warmup < 3:
         args.warmup = 3

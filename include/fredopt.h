@@ -44,7 +44,7 @@ extern "C" {
 #define FREDOPT_ERR_OOM (-6)         /* device allocation failed */
 #define FREDOPT_ERR_CUDA (-7)        /* CUDA runtime error (message via fredopt_last_error) */
 #define FREDOPT_ERR_TIMEOUT (-8)     /* a bounded device-side wait gave up */
-#define FREDOPT_ERR_UNSUPPORTED (-9) /* option not available in this build */
+#define FREDOPT_ERR_UNSUPPORTED (-9) /* option not available */
 
 /* ---- flags ---- */
 #define FREDOPT_DEVICE_PTR 0x1u /* pointer args are device pointers */
@@ -58,7 +58,7 @@ extern "C" {
 #define FREDOPT_ROWS_ROI 0x100 /* only rows of voxels in some structure are streamed;
                                   dose/LETd of the other voxels are computed at the end */
 
-/* ---- constraint kinds (Fig. 2 half-spaces; LETd limit as in the benchmark spec) ----
+/* ---- constraint kinds (Fig. 2 half-spaces; the LETd limit LETd <= Lambda as the half-space (L - Lambda D) w <= 0) ----
  * DOSE_MAX / DOSE_MIN : (D w)_i <= / >= bound                        (Gy)
  * CDL_MAX  / CDL_MIN  : c (L w)_i <= / >= bound, c = params.c_cdl    (Gy)
  * LETD_MAX / LETD_MIN : ((L - bound D) w)_i <= / >= 0, i.e. LETd_i <= / >= bound (keV/um)

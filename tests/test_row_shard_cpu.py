@@ -7,7 +7,7 @@ one all-reduce per pass.  The fluence w is replicated.  This test runs that
 exchange with two processes and the oracle's own functions on each shard, and
 checks that the all-reduced simultaneous step, gradient and objective equal
 the unsharded oracle's.  It exercises the design's arithmetic, not a GPU
-code path: each box of this build has one GPU, so the library runs replicas.
+code path: the library itself drives one GPU per process and runs replicas.
 """
 import os
 import socket
