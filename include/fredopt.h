@@ -339,6 +339,24 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);
  * -1 for a null handle. */
 int64_t fredopt_launch_count(fredopt_t h);
 
+/* Failure-detection check of the bounded device-side wait (no GPU fault
+ * involved).  Every device-side wait of the library (the mbarrier that the
+ * bulk copies of x and of the CSC windows complete) polls at most a fixed
+ * number of times; when it gives up the kernel sets the handle's device error
+ * word and returns, and the next synchronising call reports
+ * FREDOPT_ERR_TIMEOUT and clears the word.  This call runs that wait alone in
+ * one CTA on the handle's stream, on a phase that only the CTA itself can
+ * complete:
+ *   arrive != 0  the CTA arrives first; the wait succeeds; returns FREDOPT_OK.
+ *   arrive == 0  nothing arrives; after `spins` polls (0 = the bound the
+ *                kernels use) the wait gives up; returns FREDOPT_ERR_TIMEOUT
+ *                and leaves the handle usable (error word and tile counters
+ *                cleared).
+ * `elapsed_ms` (may be NULL) receives the kernel's device time, which at
+ * spins == 0 is the time a failed wait takes to give up.  Synchronises the
+ * handle's stream.  Needs no loaded plan. */
+int fredopt_check_wait(fredopt_t h, int arrive, int spins, float* elapsed_ms);
+
 /* ---- tile autotuning and batches of plans ----
  *
  * Tiles are the contiguous ranges of rows (forward product) and of column

@@ -1870,6 +1870,30 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches) {
 
 int64_t fredopt_launch_count(fredopt_t h) { return h ? h->launches : -1; }
 
+int fredopt_check_wait(fredopt_t h, int arrive, int spins, float* elapsed_ms) {
+  if (!h) return FREDOPT_ERR_INVALID_ARG;
+  if (spins < 0) return fail(h, FREDOPT_ERR_INVALID_ARG, "spins must be >= 0");
+  DeviceGuard dg(h->device);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(h, FREDOPT_ERR_CUDA, "event create");
+  }
+  cudaEventRecord(e0, h->stream);
+  launch_wait_check(arrive, spins, h->st.p, h->stream);
+  cudaError_t e = cudaGetLastError();
+  cudaEventRecord(e1, h->stream);
+  const int rc = e != cudaSuccess ? cuda_fail(h, e, "wait check launch") : check_sticky(h);
+  if (elapsed_ms) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = -1.0f;
+    *elapsed_ms = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 int fredopt_get_tuning(fredopt_t h, int64_t* row_cost, int64_t* chunk_cost) {
   int rc = need_loaded(h);
   if (rc) return rc;

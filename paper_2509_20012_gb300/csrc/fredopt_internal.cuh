@@ -252,6 +252,8 @@ void launch_sweep_pos(const int64_t* cp, const int32_t* row, int32_t n, const in
 void launch_sweep_update(const Geometry& g, int fmt, const SweepArgs& a, cudaStream_t s);
 void launch_sweep_finish(const Geometry& g, int n, const float* x, float* out, int in_solve, DevState* st,
                          LogEntry* log, cudaStream_t s);
+// One CTA in the bounded wait of the bulk copies (spins <= 0: their bound).
+void launch_wait_check(int arrive, int spins, DevState* st, cudaStream_t s);
 
 // ---- volume statistics (fredopt_volume.cu)
 constexpr int kMaxVolReq = 64;  // requests per call

@@ -1704,4 +1704,24 @@ void launch_sweep_finish(const Geometry& g, int n, const float* x, float* out, i
   k_sweep_finish<<<gb, 256, 0, s>>>(n, x, out, in_solve, st, log);
 }
 
+// Failure detection without a fault: one CTA polls an mbarrier phase with the
+// same bounded wait the bulk copies use.  With `arrive` set, thread 0 arrives
+// first and the phase completes; otherwise nothing arrives, every poll fails,
+// and after `spins` polls the CTA records the give-up in the error word and
+// returns.  No copy is ever issued on this barrier.
+__global__ void k_wait_check(int arrive, int spins, DevState* st) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_expect_tx(&bar, 0u);
+  if (!mbar_wait(&bar, 0, spins) && threadIdx.x == 0) atomicOr(&st->err, 1);
+}
+
+void launch_wait_check(int arrive, int spins, DevState* st, cudaStream_t s) {
+  k_wait_check<<<1, 32, 0, s>>>(arrive, spins > 0 ? spins : kMbarSpins, st);
+}
+
 }  // namespace fo

@@ -28,6 +28,7 @@ MAX_SWEEP_BLOCKS = 1024
 NORMS = {"all": 0, "violated": 1}
 KCLASS_N = 6
 KCLASS_NAMES = ["forward", "backward", "constraints", "colfinish", "finish", "other"]
+ERR_TIMEOUT = -8  # FREDOPT_ERR_TIMEOUT: a bounded device-side wait gave up
 
 
 class FredoptError(RuntimeError):
@@ -153,6 +154,7 @@ _SIGS = {
     "fredopt_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fredopt_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fredopt_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "fredopt_check_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "fredopt_footprint_bytes": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int]),
     "fredopt_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64,
                                              ctypes.c_int, ctypes.c_int]),
@@ -511,6 +513,17 @@ class Handle:
 
     def launch_count(self) -> int:
         return int(self.lib.fredopt_launch_count(self.h))
+
+    def check_wait(self, arrive: bool, spins: int = 0):
+        """Run the bounded device-side wait alone (fredopt_check_wait).
+        Returns (status, device ms): status 0 when the wait completed,
+        ERR_TIMEOUT when it gave up (the handle stays usable); any other
+        error raises FredoptError."""
+        ms = ctypes.c_float()
+        rc = self.lib.fredopt_check_wait(self.h, int(bool(arrive)), int(spins), ctypes.byref(ms))
+        if rc != ERR_TIMEOUT:
+            self._check(rc)
+        return rc, ms.value
 
     def autotune(self, reps: int = 3):
         """Time candidate tile weights and keep the fastest (results unchanged)."""

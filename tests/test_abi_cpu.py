@@ -60,6 +60,13 @@ def test_null_and_bad_arguments_without_gpu(lib):
     # no device with this index (and on a CPU-only machine none at all)
     assert lib.fredopt_create(ctypes.byref(h), 1 << 20, None) == -1
     assert lib.fredopt_iterate(None, 1) == -1
+    assert lib.fredopt_check_wait(None, 0, 0, None) == -1
+
+
+def test_binding_error_constant_matches_header():
+    from paper_2509_20012_gb300 import fredopt
+    text = open(os.path.join(ROOT, "include", "fredopt.h")).read()
+    assert int(re.search(r"#define FREDOPT_ERR_TIMEOUT \((-?\d+)\)", text).group(1)) == fredopt.ERR_TIMEOUT
 
 
 def test_kernels_compiled_for_sm_103a():
