@@ -121,19 +121,19 @@ class ClockSampler:
 
 # DRAM bytes per nonzero of one forward launch (dram__bytes_read.sum +
 # dram__bytes_write.sum, ncu, half-resolution clinical phantom, average of the
-# two forward launches of an iteration); traffic grows with the nonzeros, so
-# it is scaled to the full plan.  FP32 storage only; the other storages have
-# no capture yet (null).
-FWD_TRAFFIC_PER_NNZ = {"fp32": 12.48}
+# two forward launches of an iteration), keyed by (storage, index bytes);
+# traffic grows with the nonzeros, so it is scaled to the full plan.  A
+# stream without a capture reports null.
+FWD_TRAFFIC_PER_NNZ = {("fp32", 4): 12.48}
 
 
-def fwd_bytes(nnz, rows, vb, n_launch_obj, n_launch_bc):
+def fwd_bytes(nnz, rows, vb, ib, n_launch_obj, n_launch_bc):
     """Algorithmic bytes of the forward launches: the shared index stream
-    (4 B) and both value streams (vb B each) per nonzero; per row with
-    nonzeros: row_ptr (8 B), the (Dx, Lx) pair (8 B), mask (4 B) and the
+    (ib = 2 or 4 B) and both value streams (vb B each) per nonzero; per row
+    with nonzeros: row_ptr (8 B), the (Dx, Lx) pair (8 B), mask (4 B) and the
     residual pair written (OBJ) or read (BC) (8 B).  16-bit storage adds the
     two row scales (8 B)."""
-    base = nnz * (4 + 2 * vb) + rows * (8 + 8 + 12 + (8 if vb == 2 else 0))
+    base = nnz * (ib + 2 * vb) + rows * (8 + 8 + 12 + (8 if vb == 2 else 0))
     return (n_launch_obj + n_launch_bc) * base
 
 
@@ -178,6 +178,7 @@ def run_gpu_arm(args):
         h.load_plan(plan, fmt=fmt, rows=rows)
         t_load = time.perf_counter() - t0
         sz = h.sizes()
+        ib = h.storage()[0]
         # plain launches with CUDA events around every kernel on the library stream
         h.set_timing(True)
         h.begin(plan.w0, plan.alpha, plan.relaxation)
@@ -209,20 +210,21 @@ def run_gpu_arm(args):
         n_iter = args.steps
         hot = np.ones(plan.n_vox, bool) if rows == "all" else plan.mask != 0
         rows_nz = int(np.count_nonzero(hot & (np.diff(plan.row_ptr) > 0)))
-        fb = fwd_bytes(sz["nnz_rows"], rows_nz, vb, n_iter, n_iter)
+        fb = fwd_bytes(sz["nnz_rows"], rows_nz, vb, ib, n_iter, n_iter)
         # chunk count is internal; it is small next to nnz (bounded by nnz/256 + n_spots)
         n_chunks_est = sz["nnz_rows"] // 2048 + sz["n_spots"]
         bb = bwd_bytes(sz["nnz_rows"], rows_nz, n_chunks_est, vb, n_iter, n_iter)
         f_ms, b_ms = kt["forward"][0], kt["backward"][0]
         fw = {"bound": "hbm", "achieved": fb / (f_ms * 1e-3) / 1e9 if f_ms else None, "peak": hbm,
-              "unit": "GB/s", "kernel": "k_forward (fused Dx/Lx)", "launches": nf, "ms_total": f_ms,
+              "unit": "GB/s", "kernel": "k_forward (fused Dx/Lx)", "index_bytes": ib, "launches": nf,
+              "ms_total": f_ms,
               "bytes_per_launch": fb / max(1, 2 * n_iter)}
         bw = {"bound": "hbm", "achieved": bb / (b_ms * 1e-3) / 1e9 if b_ms else None, "peak": hbm,
               "unit": "GB/s", "kernel": "k_backward (CSC chunks)", "launches": nb, "ms_total": b_ms,
               "bytes_per_launch": bb / max(1, 2 * n_iter)}
         for r in (fw, bw):
             r["frac"] = r["achieved"] / hbm if r["achieved"] else None
-        t = FWD_TRAFFIC_PER_NNZ.get(fmt)
+        t = FWD_TRAFFIC_PER_NNZ.get((fmt, ib))
         fw["traffic"] = t * sz["nnz_rows"] if t else None
         bw["traffic"] = None
         return dict(ms=ms, kt=kt, launches=launches, clocks=clocks, rep=rep, sizes=sz, t_load=t_load,
@@ -516,6 +518,7 @@ def batching_benchmark(args, local):
             h.load_plan(rp, fmt="bf16")
             t_load = time.perf_counter() - t
             tune = h.autotune(reps=2)
+            ib = h.storage()[0]
             h.set_timing(True)
             h.begin(rp.w0, rp.alpha, rp.relaxation)
             h.iterate(3)
@@ -527,10 +530,11 @@ def batching_benchmark(args, local):
         ms = sum(v[0] for v in kt.values())
         hbm, _ = peaks()
         fb = kt["forward"][0]
-        f_bytes = 2 * iters * (rp.nnz * 8 + int(np.count_nonzero(np.diff(rp.row_ptr) > 0)) * 36)
+        f_bytes = 2 * iters * (rp.nnz * (ib + 4) + int(np.count_nonzero(np.diff(rp.row_ptr) > 0)) * 36)
         out["robust_stacked"] = {
             "scenarios": len(per), "nnz_per_scenario_matrix": int(np.mean(per)), "nnz_stacked": int(rp.nnz),
-            "rows_stacked": int(rp.n_vox), "n_spots": int(rp.n_spots), "storage": "bf16", "tiles": tune,
+            "rows_stacked": int(rp.n_vox), "n_spots": int(rp.n_spots), "storage": "bf16", "index_bytes": ib,
+            "tiles": tune,
             "iters_per_s": iters / (ms * 1e-3), "forward_GBps": f_bytes / (fb * 1e-3) / 1e9,
             "forward_frac_of_hbm": f_bytes / (fb * 1e-3) / 1e9 / hbm,
             "generate_s": round(t_gen, 1), "load_s": round(t_load, 2),

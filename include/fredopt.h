@@ -57,6 +57,12 @@ extern "C" {
 #define FREDOPT_ROWS_ALL 0x000 /* every voxel row is streamed every pass (default) */
 #define FREDOPT_ROWS_ROI 0x100 /* only rows of voxels in some structure are streamed;
                                   dose/LETd of the other voxels are computed at the end */
+/* index width of the forward stream (or'ed into `format`): by default the
+ * column indices are kept as 16-bit values when n_spots <= 65536 and the
+ * fluence fits the forward kernel's shared memory (about 58000 spots on
+ * GB300), which saves 2 bytes per nonzero and pass with identical results;
+ * FREDOPT_INDEX32 keeps them 32-bit. */
+#define FREDOPT_INDEX32 0x200
 
 /* ---- constraint kinds (Fig. 2 half-spaces; the LETd limit LETd <= Lambda as the half-space (L - Lambda D) w <= 0) ----
  * DOSE_MAX / DOSE_MIN : (D w)_i <= / >= bound                        (Gy)
@@ -166,7 +172,8 @@ int fredopt_destroy(fredopt_t h);
  * Table 2).  row_ptr int64[n_vox+1] with row_ptr[0] = 0 and row_ptr[n_vox] =
  * nnz; col int32[nnz] strictly increasing within a row, 0 <= col < n_spots;
  * D_val, L_val float[nnz] finite; voxel_mask uint32[n_vox] (bit b: voxel in
- * structure b).  `format` = FREDOPT_FP32|BF16|FP16 | FREDOPT_ROWS_ALL|ROI.
+ * structure b).  `format` = FREDOPT_FP32|BF16|FP16 | FREDOPT_ROWS_ALL|ROI
+ * [| FREDOPT_INDEX32].
  * The data is validated on the device (FREDOPT_ERR_PATTERN / NONFINITE),
  * the CSC copy of the streamed rows is built (values moved bit-exactly), the
  * values are quantised if asked, and the FP64 row moments |D_i|^2, |L_i|^2,
@@ -318,6 +325,10 @@ int fredopt_get_sizes(fredopt_t h, int64_t* n_vox, int64_t* n_spots, int64_t* nn
  * (uint32[n_rows]) in device order. Host pointers. */
 int fredopt_get_rows(fredopt_t h, int64_t* voxel, uint32_t* mask);
 
+/* Stored widths of the loaded plan: bytes per column index of the forward
+ * stream (2 or 4, see FREDOPT_INDEX32) and per stored value (4 or 2). */
+int fredopt_get_storage(fredopt_t h, int* index_bytes, int* value_bytes);
+
 /* The CSC copy of the streamed rows: col_ptr int64[n_spots+1], row (index
  * into the streamed rows) int32[nnz_rows], D and L values float[nnz_rows]
  * (dequantised: scale * stored value for BF16/FP16). Host pointers. */
@@ -339,17 +350,21 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);
  * -1 for a null handle. */
 int64_t fredopt_launch_count(fredopt_t h);
 
+/* Polls of one device-side wait before it gives up: about 1 s on GB300
+ * (a failed poll suspends about 4 us); a bulk copy completes in microseconds. */
+#define FREDOPT_WAIT_POLLS (1 << 18)
+
 /* Failure-detection check of the bounded device-side wait (no GPU fault
  * involved).  Every device-side wait of the library (the mbarrier that the
- * bulk copies of x and of the CSC windows complete) polls at most a fixed
- * number of times; when it gives up the kernel sets the handle's device error
+ * bulk copies of x and of the CSC windows complete) polls at most
+ * FREDOPT_WAIT_POLLS times; when it gives up the kernel sets the handle's device error
  * word and returns, and the next synchronising call reports
  * FREDOPT_ERR_TIMEOUT and clears the word.  This call runs that wait alone in
  * one CTA on the handle's stream, on a phase that only the CTA itself can
  * complete:
  *   arrive != 0  the CTA arrives first; the wait succeeds; returns FREDOPT_OK.
  *   arrive == 0  nothing arrives; after `spins` polls (0 = the bound the
- *                kernels use) the wait gives up; returns FREDOPT_ERR_TIMEOUT
+ *                kernels use, FREDOPT_WAIT_POLLS) the wait gives up; returns FREDOPT_ERR_TIMEOUT
  *                and leaves the handle usable (error word and tile counters
  *                cleared).
  * `elapsed_ms` (may be NULL) receives the kernel's device time, which at

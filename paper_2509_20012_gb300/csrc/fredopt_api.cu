@@ -73,6 +73,7 @@ struct fredopt_ctx {
   int32_t n = 0, n_pad = 0;
   DBuf<int64_t> rp;
   DBuf<int32_t> col;
+  DBuf<uint16_t> col16;  // 16-bit copy of col for the forward stream (col then freed)
   DBuf<uint8_t> Dv, Lv;
   DBuf<float> sD, sL;
   DBuf<int64_t> voxel;  // device row -> voxel (when perm)
@@ -346,6 +347,7 @@ FwdArgs fwd_args(fredopt_t h, bool hot) {
   FwdArgs a{};
   a.rp = h->rp.p;
   a.col = h->col.p;
+  a.col16 = h->col16.p;
   a.Dv = h->Dv.p;
   a.Lv = h->Lv.p;
   a.sD = h->fmt ? h->sD.p : nullptr;
@@ -837,8 +839,8 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   if (!h) return FREDOPT_ERR_INVALID_ARG;
   const int fmt = format & 0xff;
   const bool roi = (format & FREDOPT_ROWS_ROI) != 0;
-  if (fmt < 0 || fmt > 2 || (format & ~0x1ff))
-    return fail(h, FREDOPT_ERR_INVALID_ARG, "format must be FP32/BF16/FP16 | ROWS_ALL/ROI");
+  if (fmt < 0 || fmt > 2 || (format & ~0x3ff))
+    return fail(h, FREDOPT_ERR_INVALID_ARG, "format must be FP32/BF16/FP16 | ROWS_ALL/ROI | INDEX32");
   if (n_vox < 0 || n_spots < 1 || nnz < 0 || nnz > 2147483647LL || n_vox > 2147483647LL)
     return fail(h, FREDOPT_ERR_SHAPE, "need n_vox >= 0, n_spots >= 1, 0 <= nnz < 2^31");
   if (!row_ptr || !voxel_mask || (nnz > 0 && (!col || !D_val || !L_val)))
@@ -950,7 +952,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   if (verr & 2) return fail(h, FREDOPT_ERR_NONFINITE, "NaN or Inf in D or L");
 
   // ---- drop the previous plan
-  h->rp.release(); h->col.release(); h->Dv.release(); h->Lv.release(); h->sD.release(); h->sL.release();
+  h->rp.release(); h->col.release(); h->col16.release(); h->Dv.release(); h->Lv.release(); h->sD.release(); h->sL.release();
   h->voxel.release(); h->mask.release(); h->cp.release(); h->crow.release(); h->DTv.release(); h->LTv.release();
 
   // ---- FP32 CSR in device order (zero padded)
@@ -1083,6 +1085,17 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     if (rc) return rc;
   }
 
+  // ---- 16-bit column indices for the forward stream: 2 bytes less per
+  // nonzero, same sums.  Only with x staged in shared memory (that bounds
+  // n_spots below 65536); the int32 copy served the CSC build and goes.
+  if (!(format & FREDOPT_INDEX32) && n_spots <= 65536 && forward_uses_smem(h->geo, h->n_pad)) {
+    CK(h->col16.alloc(h->col.n));
+    launch_narrow_idx(h->col.p, h->col16.p, (int64_t)h->col.n, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    h->col.release();
+  }
+
   // ---- row schedules of the forward product (rows with nonzeros only);
   // a row end (two warp reductions and bookkeeping) costs about as much as
   // streaming FO_ROW_COST nonzeros (fredopt_autotune can pick another weight)
@@ -1101,7 +1114,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   rc = set_fwd_schedule(h, FO_ROW_COST);
   if (rc) return rc;
   // streaming (evict-first) loads when the streamed matrices do not fit in L2
-  const double mat_bytes = (double)h->nnz_hot * (4.0 + 2.0 * value_bytes(fmt));
+  const double mat_bytes = (double)h->nnz_hot * ((h->col16.p ? 2.0 : 4.0) + 2.0 * value_bytes(fmt));
 #ifndef FO_STREAM_HINT
 #define FO_STREAM_HINT -1
 #endif
@@ -1792,6 +1805,14 @@ int fredopt_get_sizes(fredopt_t h, int64_t* n_vox, int64_t* n_spots, int64_t* nn
   if (nnz) *nnz = h->nnz;
   if (n_rows) *n_rows = h->n_hot;
   if (nnz_rows) *nnz_rows = h->nnz_hot;
+  return FREDOPT_OK;
+}
+
+int fredopt_get_storage(fredopt_t h, int* index_bytes, int* val_bytes) {
+  int rc = need_loaded(h);
+  if (rc) return rc;
+  if (index_bytes) *index_bytes = h->col16.p ? 2 : 4;
+  if (val_bytes) *val_bytes = value_bytes(h->fmt);
   return FREDOPT_OK;
 }
 

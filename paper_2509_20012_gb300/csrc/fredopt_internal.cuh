@@ -2,7 +2,9 @@
 // Device data layout (all in HBM).  Device order of rows: streamed rows with
 // nonzeros, streamed rows without, other rows with nonzeros, other rows
 // without (each group ascending by voxel; see fredopt_api.cu):
-//   CSR   rp int64[V+1], col int32[nnz], Dv/Lv VT[nnz], sD/sL float[V] (16-bit only);
+//   CSR   rp int64[V+1], col int32[nnz] or col16 uint16[nnz] (n <= 65536 with x
+//         staged in shared memory; the int32 copy is then freed after the CSC
+//         build), Dv/Lv VT[nnz], sD/sL float[V] (16-bit only);
 //         col/D/L zero padded so whole 32*16-byte blocks past the end stay in bounds
 //   CSC   cp int64[n+1], row int32[nnz_hot] (index of a streamed row), DTv/LTv VT[nnz_hot]
 //   rows  voxel int64[V] (device row -> voxel), mask uint32[n_hot],
@@ -78,7 +80,8 @@ enum ColMode { COL_OUT = 0, COL_GRAD = 1, COL_PROJ = 2 };
 
 struct FwdArgs {
   const int64_t* rp;
-  const int32_t* col;
+  const int32_t* col;     // column indices, or null when col16 is set
+  const uint16_t* col16;  // 16-bit column indices (x staged in shared memory only)
   const void* Dv;
   const void* Lv;
   const float* sD;       // row scales (16-bit storage) or null
@@ -252,6 +255,8 @@ void launch_sweep_pos(const int64_t* cp, const int32_t* row, int32_t n, const in
 void launch_sweep_update(const Geometry& g, int fmt, const SweepArgs& a, cudaStream_t s);
 void launch_sweep_finish(const Geometry& g, int n, const float* x, float* out, int in_solve, DevState* st,
                          LogEntry* log, cudaStream_t s);
+// out[i] = in[i] for i < n (in[i] < 65536), n a multiple of 4.
+void launch_narrow_idx(const int32_t* in, uint16_t* out, int64_t n, cudaStream_t s);
 // One CTA in the bounded wait of the bulk copies (spins <= 0: their bound).
 void launch_wait_check(int arrive, int spins, DevState* st, cudaStream_t s);
 

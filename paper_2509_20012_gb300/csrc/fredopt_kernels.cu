@@ -21,6 +21,7 @@
 //                    the closed-form non-ascent trial loop (Fig. 3).
 //   K5 setup         validation, row gather, quantisation, FP64 moments,
 //                    blocked stable counting transpose (CSR -> CSC).
+#include "fredopt.h"
 #include "fredopt_internal.cuh"
 
 #include <algorithm>
@@ -63,7 +64,7 @@ constexpr int kPrefetchUnits = FO_PREFETCH_UNITS;
 constexpr int kBwdThreads = 256;
 constexpr int kRowThreads = 256;
 constexpr int kColThreads = 256;
-constexpr int kMbarSpins = 1 << 22;
+constexpr int kMbarSpins = FREDOPT_WAIT_POLLS;
 
 // ------------------------------------------------------------------ helpers
 
@@ -247,12 +248,33 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int ma
 
 // ------------------------------------------------------------------ streaming core
 
-// One 16-byte-per-lane block of the index stream and the two value streams.
+// One block of the index stream and the two value streams, 4 elements per
+// lane: 16 bytes of 32-bit indices (8 bytes of 16-bit ones, in c0.x, c0.y)
+// and 16 bytes of FP32 values (8 bytes of 16-bit ones, in the low half).
 template <typename VT>
 struct Blk {
   int4 c0;      // 4 indices
-  uint4 a, b;   // values of the two streams (16-bit: low 8 bytes)
+  uint4 a, b;   // values of the two streams
 };
+
+template <bool S>
+__device__ __forceinline__ int4 ld_idx(const int32_t* p) {
+  return ld16<S>(reinterpret_cast<const int4*>(p));
+}
+template <bool S>
+__device__ __forceinline__ int4 ld_idx(const uint16_t* p) {  // 4 x 16-bit = 8 bytes
+  uint2 v;
+  if (S) v = __ldcs(reinterpret_cast<const uint2*>(p));
+  else v = __ldg(reinterpret_cast<const uint2*>(p));
+  return make_int4((int)v.x, (int)v.y, 0, 0);
+}
+__device__ __forceinline__ void unpack_idx(int32_t, int4 c, int* cs) {
+  cs[0] = c.x; cs[1] = c.y; cs[2] = c.z; cs[3] = c.w;
+}
+__device__ __forceinline__ void unpack_idx(uint16_t, int4 c, int* cs) {  // little-endian halves
+  cs[0] = (int)((uint32_t)c.x & 0xffffu); cs[1] = (int)((uint32_t)c.x >> 16);
+  cs[2] = (int)((uint32_t)c.y & 0xffffu); cs[3] = (int)((uint32_t)c.y >> 16);
+}
 
 template <bool S>
 __device__ __forceinline__ uint4 ld_vals(const float* p) {
@@ -266,10 +288,10 @@ __device__ __forceinline__ uint4 ld_vals(const H* p) {  // 4 x 16-bit = 8 bytes
   return make_uint4(v.x, v.y, 0u, 0u);
 }
 
-template <typename VT, bool S, bool USE_A>
-__device__ __forceinline__ void load_blk(Blk<VT>& k, const int32_t* idx, const VT* Av, const VT* Bv,
+template <typename VT, bool S, bool USE_A, typename IT>
+__device__ __forceinline__ void load_blk(Blk<VT>& k, const IT* idx, const VT* Av, const VT* Bv,
                                          int64_t p) {
-  k.c0 = ld16<S>(reinterpret_cast<const int4*>(idx + p));
+  k.c0 = ld_idx<S>(idx + p);
   if (USE_A) k.a = ld_vals<S>(Av + p);
   k.b = ld_vals<S>(Bv + p);
 }
@@ -282,13 +304,14 @@ __device__ __forceinline__ void load_blk(Blk<VT>& k, const int32_t* idx, const V
 // sB += B_i * g(c).y.  A finished segment is summed over the warp in a fixed
 // butterfly; lane (r - base) keeps it; every 32 segments (and at the end)
 // flush(base, count, mine_A, mine_B) runs with lane j < count owning segment
-// base + j.  Deterministic: the split depends only on ptr, r0, r1.
+// base + j.  Deterministic: the split depends only on ptr, r0, r1.  The index
+// stream is int32 or uint16 (IT); the sums do not depend on its width.
 // The arrays must be readable (zero padded) up to
 // round_up(ptr[r1], 32*V) + U*32*V elements (a prefetch starts below ptr[r1]
 // and covers U*32*V elements, within the same bound).
-template <typename VT, typename Acc, bool S, bool USE_A, int U, class Gather, class Flush,
+template <typename VT, typename Acc, bool S, bool USE_A, int U, typename IT, class Gather, class Flush,
           int PF = kPrefetchUnits, bool PP = false>
-__device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
+__device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
                                                 const VT* __restrict__ Av, const VT* __restrict__ Bv,
                                                 const int64_t* __restrict__ ptr, int64_t r0, int64_t r1,
                                                 int lane, Gather gather, Flush flush) {
@@ -319,7 +342,7 @@ __device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
       const int e0 = bb + lane * V;
       int cs[V];
       float av[V], bv[V];
-      cs[0] = unit[u].c0.x; cs[1] = unit[u].c0.y; cs[2] = unit[u].c0.z; cs[3] = unit[u].c0.w;
+      unpack_idx(IT(), unit[u].c0, cs);
       if (USE_A) unpack(VT(), unit[u].a, av);
       unpack(VT(), unit[u].b, bv);
       float2 gv[V];
@@ -358,7 +381,7 @@ __device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
   // the demand loads of the warp mostly wait on L2 rather than DRAM
   auto prefetch_unit = [&](int q) {
     if (PF > 0 && lane == 0 && q < pe) {
-      bulk_prefetch_l2(idx + q, (uint32_t)(UB * sizeof(int32_t)));
+      bulk_prefetch_l2(idx + q, (uint32_t)(UB * sizeof(IT)));
       if (USE_A) bulk_prefetch_l2(Av + q, (uint32_t)(UB * sizeof(VT)));
       bulk_prefetch_l2(Bv + q, (uint32_t)(UB * sizeof(VT)));
     }
@@ -366,7 +389,7 @@ __device__ __forceinline__ void stream_segments(const int32_t* __restrict__ idx,
   auto load_unit = [&](Blk<VT>* unit, int b) {
     prefetch_unit(b + PF * UB);
 #pragma unroll
-    for (int u = 0; u < U; ++u) load_blk<VT, S, USE_A>(unit[u], idx, Av, Bv, b + u * BLK + lane * V);
+    for (int u = 0; u < U; ++u) load_blk<VT, S, USE_A, IT>(unit[u], idx, Av, Bv, b + u * BLK + lane * V);
   };
 
   int b = 0;
@@ -421,8 +444,13 @@ __device__ __forceinline__ void row_objective(const Tables& t, uint32_t m, doubl
   }
 }
 
+template <typename IT> __device__ __forceinline__ const IT* fwd_col(const FwdArgs& a);
+template <> __device__ __forceinline__ const int32_t* fwd_col<int32_t>(const FwdArgs& a) { return a.col; }
+template <> __device__ __forceinline__ const uint16_t* fwd_col<uint16_t>(const FwdArgs& a) { return a.col16; }
+
 // Fused Dx, Lx over the warp's nonempty rows [warp_row[2w], warp_row[2w+1]).
-template <typename VT, int EPI, bool XS, bool S>
+// IT: width of the column indices (uint16_t only with x in shared memory).
+template <typename VT, int EPI, bool XS, bool S, typename IT>
 __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(FwdArgs a, Tables t) {
   extern __shared__ __align__(128) unsigned char smem[];
   using Acc = typename std::conditional<EPI == EPI_FINAL, DF, float>::type;
@@ -505,8 +533,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(Fwd
     const int64_t r0 = a.warp_row[2 * job], r1 = a.warp_row[2 * job + 1];
     acc0 = 0.0;
     acc1 = 0.0;
-    stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : kFwdUnroll16)>(a.col, Dv, Lv, a.rp, r0, r1,
-                                                                            lane, gather, flush);
+    stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : kFwdUnroll16)>(fwd_col<IT>(a), Dv, Lv, a.rp,
+                                                                            r0, r1, lane, gather, flush);
     if (EPI == EPI_OBJ || EPI == EPI_BC) {  // partials per tile, summed later in tile order
       const double s0 = warp_sum(acc0), s1 = warp_sum(acc1);
       if (lane == 0) {
@@ -1268,18 +1296,23 @@ __global__ void k_scatter_y(const float2* y, const int64_t* voxel, int64_t n, fl
 
 // ------------------------------------------------------------------ launch wrappers
 
-template <typename VT, int EPI, bool XS, bool S>
+template <typename VT, int EPI, bool XS, bool S, typename IT = int32_t>
 static void fwd_inst(const Geometry& g, const FwdArgs& a, const Tables& t, cudaStream_t s) {
   const size_t smem = XS ? (size_t)a.n_x_pad * sizeof(float) + 16 : 0;
   // only the CTAs that hold scheduled warps (all of them for a full pass)
   const int wpb = g.fwd_threads / 32;
   const int blocks = std::max(1, std::min(g.fwd_blocks, (a.n_warps + wpb - 1) / wpb));
-  k_forward<VT, EPI, XS, S><<<blocks, g.fwd_threads, smem, s>>>(a, t);
+  k_forward<VT, EPI, XS, S, IT><<<blocks, g.fwd_threads, smem, s>>>(a, t);
 }
 
 template <typename VT, int EPI>
 static void fwd_dispatch_xs(const Geometry& g, bool xs, bool st, const FwdArgs& a, const Tables& t,
                             cudaStream_t s) {
+  if (a.col16) {  // the load keeps 16-bit indices only when x fits shared memory
+    if (EPI == EPI_FINAL || !st) fwd_inst<VT, EPI, true, false, uint16_t>(g, a, t, s);
+    else fwd_inst<VT, EPI, true, true, uint16_t>(g, a, t, s);
+    return;
+  }
   if (EPI == EPI_FINAL) {
     if (xs) fwd_inst<VT, EPI, true, false>(g, a, t, s);
     else fwd_inst<VT, EPI, false, false>(g, a, t, s);
@@ -1518,15 +1551,21 @@ void launch_scale_coef(int64_t n, const float* aD, const float* aL, const int64_
 
 // ------------------------------------------------------------------ init
 
-template <typename VT, int EPI>
-static cudaError_t set_smem_attr(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_forward<VT, EPI, true, false>,
+template <typename VT, int EPI, typename IT>
+static cudaError_t set_smem_attr_it(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_forward<VT, EPI, true, false, IT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   if (EPI != EPI_FINAL)
-    e = cudaFuncSetAttribute(k_forward<VT, EPI, true, true>,
+    e = cudaFuncSetAttribute(k_forward<VT, EPI, true, true, IT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
+}
+template <typename VT, int EPI>
+static cudaError_t set_smem_attr(int bytes) {
+  cudaError_t e = set_smem_attr_it<VT, EPI, int32_t>(bytes);
+  if (e != cudaSuccess) return e;
+  return set_smem_attr_it<VT, EPI, uint16_t>(bytes);
 }
 
 template <typename VT>
@@ -1702,6 +1741,22 @@ void launch_sweep_finish(const Geometry& g, int n, const float* x, float* out, i
                          LogEntry* log, cudaStream_t s) {
   const unsigned gb = (unsigned)std::max(1, std::min(g.n_sms, (n + 255) / 256));
   k_sweep_finish<<<gb, 256, 0, s>>>(n, x, out, in_solve, st, log);
+}
+
+__global__ void __launch_bounds__(256) k_narrow_idx(const int4* __restrict__ in, uint2* __restrict__ out, int64_t n4) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const int4 v = __ldcs(in + i);
+    out[i] = make_uint2(((uint32_t)v.x & 0xffffu) | ((uint32_t)v.y << 16),
+                        ((uint32_t)v.z & 0xffffu) | ((uint32_t)v.w << 16));
+  }
+}
+
+void launch_narrow_idx(const int32_t* in, uint16_t* out, int64_t n, cudaStream_t s) {
+  const int64_t n4 = n / 4;
+  if (n4 == 0) return;
+  const unsigned grid = (unsigned)std::min<int64_t>((n4 + 255) / 256, 152 * 8);
+  k_narrow_idx<<<grid, 256, 0, s>>>(reinterpret_cast<const int4*>(in), reinterpret_cast<uint2*>(out), n4);
 }
 
 // Failure detection without a fault: one CTA polls an mbarrier phase with the

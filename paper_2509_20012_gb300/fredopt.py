@@ -21,6 +21,7 @@ OK = 0
 DEVICE_PTR = 0x1
 FORMATS = {"fp32": 0, "bf16": 1, "fp16": 2}
 ROWS = {"all": 0x000, "roi": 0x100}
+INDEX32 = 0x200  # keep 32-bit column indices in the forward stream
 KINDS = {"DOSE_MIN": 0, "DOSE_MAX": 1, "CDL_MIN": 2, "CDL_MAX": 3, "LETD_MIN": 4, "LETD_MAX": 5}
 QUANTITIES = {"DOSE": 0, "CDL": 1, "LETD": 2}  # LETD: volume statistics only
 VOLUME_MAX_REQUESTS, VOLUME_MAX_BINS, VOLUME_MAX_FRACS = 64, 16384, 64
@@ -29,6 +30,7 @@ NORMS = {"all": 0, "violated": 1}
 KCLASS_N = 6
 KCLASS_NAMES = ["forward", "backward", "constraints", "colfinish", "finish", "other"]
 ERR_TIMEOUT = -8  # FREDOPT_ERR_TIMEOUT: a bounded device-side wait gave up
+WAIT_POLLS = 1 << 18  # FREDOPT_WAIT_POLLS
 
 
 class FredoptError(RuntimeError):
@@ -154,6 +156,7 @@ _SIGS = {
     "fredopt_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fredopt_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fredopt_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "fredopt_get_storage": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "fredopt_check_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "fredopt_footprint_bytes": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int]),
     "fredopt_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64,
@@ -282,7 +285,7 @@ class Handle:
         return rc
 
     # ---------------------------------------------------------- plan
-    def load_influence(self, row_ptr, col, D, L, mask, n_spots, fmt="fp32", rows="all"):
+    def load_influence(self, row_ptr, col, D, L, mask, n_spots, fmt="fp32", rows="all", index32=False):
         dev = _on_device(row_ptr)
         n_vox = int(row_ptr.shape[0]) - 1
         nnz = int(col.shape[0])
@@ -291,7 +294,7 @@ class Handle:
         p_d, k3 = _ptr(D, np.float32)
         p_l, k4 = _ptr(L, np.float32)
         p_m, k5 = _ptr(mask, np.uint32)
-        code = FORMATS[fmt] | ROWS[rows]
+        code = FORMATS[fmt] | ROWS[rows] | (INDEX32 if index32 else 0)
         self._check(self.lib.fredopt_load_influence(self.h, n_vox, int(n_spots), nnz, p_rp, p_c, p_d, p_l,
                                                     p_m, code, DEVICE_PTR if dev else 0))
         self.n_vox, self.n_spots = n_vox, int(n_spots)
@@ -309,11 +312,18 @@ class Handle:
                                    float(t["weight"]))
         self._check(self.lib.fredopt_set_objective(self.h, len(terms), arr))
 
-    def load_plan(self, plan, fmt="fp32", rows="all"):
+    def load_plan(self, plan, fmt="fp32", rows="all", index32=False):
         """Load a phantom.Plan-like object (row_ptr, col, D, L, mask, constraints, objective)."""
-        self.load_influence(plan.row_ptr, plan.col, plan.D, plan.L, plan.mask, plan.n_spots, fmt=fmt, rows=rows)
+        self.load_influence(plan.row_ptr, plan.col, plan.D, plan.L, plan.mask, plan.n_spots, fmt=fmt, rows=rows,
+                            index32=index32)
         self.set_constraints(plan.constraints)
         self.set_objective(plan.objective)
+
+    def storage(self):
+        """(index bytes, value bytes) of the loaded plan's forward stream."""
+        ib, vb = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.fredopt_get_storage(self.h, ctypes.byref(ib), ctypes.byref(vb)))
+        return ib.value, vb.value
 
     def sizes(self):
         v = [ctypes.c_int64() for _ in range(5)]

@@ -67,6 +67,7 @@ def test_binding_error_constant_matches_header():
     from paper_2509_20012_gb300 import fredopt
     text = open(os.path.join(ROOT, "include", "fredopt.h")).read()
     assert int(re.search(r"#define FREDOPT_ERR_TIMEOUT \((-?\d+)\)", text).group(1)) == fredopt.ERR_TIMEOUT
+    assert 1 << int(re.search(r"#define FREDOPT_WAIT_POLLS \(1 << (\d+)\)", text).group(1)) == fredopt.WAIT_POLLS
 
 
 def test_kernels_compiled_for_sm_103a():

@@ -332,6 +332,50 @@ def test_claimed_tiles_equal_static_tiles(lib, tiny, rows):
     assert log2 == log1
 
 
+@pytest.mark.parametrize("fmt", ["fp32", "bf16"])
+@pytest.mark.parametrize("rows", ["all", "roi"])
+def test_index16_equals_index32(lib, tiny, fmt, rows):
+    """16-bit column indices (the default when the spots fit) and 32-bit ones
+    stream the same elements in the same order: forward products, sweeps,
+    iterates, logs and final outputs are bit-identical."""
+    pl, P, R = tiny
+    x = np.random.default_rng(11).uniform(0.0, 2.0, pl.n_spots).astype(np.float32)
+    out = []
+    for index32 in (False, True):
+        with lib.Handle(0) as h:
+            h.load_plan(pl, fmt=fmt, rows=rows, index32=index32)
+            assert h.storage() == (4 if index32 else 2, 4 if fmt == "fp32" else 2)
+            dose, lw = h.forward(x)
+            sw = h.sweep_step(x, 16)
+            w, d, l, rep = h.superiorize(pl.w0, 15, pl.alpha, pl.relaxation)
+            out.append((dose, lw, sw, w, d, l, h.get_log()))
+    a, b = out
+    for u, v in zip(a[:6], b[:6]):
+        np.testing.assert_array_equal(u, v)
+    assert a[6] == b[6]
+
+
+@pytest.mark.parametrize("n_cols,index_bytes", [(1, 2), (58000, 2), (60000, 4), (70000, 4)])
+def test_index_width_by_spot_count(lib, n_cols, index_bytes):
+    """16-bit indices need x in the forward kernel's shared memory (up to about
+    58000 spots); past that the forward keeps 32-bit indices and reads x
+    through L1.  Both match FP64 products of the CSR rows."""
+    rp, col, D, L = phantom.random_csr(300, n_cols, min(0.5, 40.0 / n_cols), seed=n_cols, empty_rows=7)
+    mask = np.ones(300, np.uint32)
+    x = np.random.default_rng(2).uniform(0.0, 2.0, n_cols).astype(np.float32)
+    with lib.Handle(0) as h:
+        h.load_influence(rp, col, D, L, mask, n_cols)
+        assert h.storage()[0] == index_bytes
+        dose, lw = h.forward(x)
+    x64 = x.astype(np.float64)
+    for i in range(300):
+        s, e = rp[i], rp[i + 1]
+        d_ref = D[s:e].astype(np.float64) @ x64[col[s:e]]
+        l_ref = L[s:e].astype(np.float64) @ x64[col[s:e]]
+        assert abs(dose[i] - d_ref) <= 1e-5 * abs(d_ref) + 1e-30
+        assert abs(lw[i] - l_ref) <= 1e-5 * abs(l_ref) + 1e-30
+
+
 def test_checkpoint_resume_bit_exact(lib, tiny):
     pl, P, R = tiny
     with handle(lib, pl) as h:
