@@ -124,7 +124,7 @@ class ClockSampler:
 # two forward launches of an iteration), keyed by (storage, index bytes);
 # traffic grows with the nonzeros, so it is scaled to the full plan.  A
 # stream without a capture reports null.
-FWD_TRAFFIC_PER_NNZ = {("fp32", 4): 12.48}
+FWD_TRAFFIC_PER_NNZ = {("fp32", 4): 12.48, ("fp32", 2): 10.17}
 
 
 def fwd_bytes(nnz, rows, vb, ib, n_launch_obj, n_launch_bc):
@@ -137,13 +137,16 @@ def fwd_bytes(nnz, rows, vb, ib, n_launch_obj, n_launch_bc):
     return (n_launch_obj + n_launch_bc) * base
 
 
-def bwd_bytes(nnz, n_hot, n_chunks, vb, n_grad, n_proj):
-    """Transposed launches: row index (4 B) + L (vb) [+ D (vb) for the
-    projection pass, and for a gradient with DOSE terms] per nonzero, the
+def bwd_bytes(nnz, n_hot, n_chunks, vb, rb, n_grad, n_proj):
+    """Transposed launches: row index (rb = 2 or 4 B) + L (vb) [+ D (vb) for
+    the projection pass, and for a gradient with DOSE terms] per nonzero, the
     coefficient pair read once per row with nonzeros (8 B), chunk pointer
-    (8 B) and chunk sum (4 B) per chunk."""
-    g = nnz * (4 + vb) + n_hot * 8 + n_chunks * 12
-    p = nnz * (4 + 2 * vb) + n_hot * 8 + n_chunks * 12
+    (8 B) and chunk sum (4 B) per chunk.  Based 16-bit rows also read a 4 B
+    base per 128 nonzeros (and 512 B per wide block, an encoding cost left
+    out here)."""
+    hdr = nnz // 128 * 4 if rb == 2 else 0
+    g = nnz * (rb + vb) + hdr + n_hot * 8 + n_chunks * 12
+    p = nnz * (rb + 2 * vb) + hdr + n_hot * 8 + n_chunks * 12
     return n_grad * g + n_proj * p
 
 
@@ -178,7 +181,7 @@ def run_gpu_arm(args):
         h.load_plan(plan, fmt=fmt, rows=rows)
         t_load = time.perf_counter() - t0
         sz = h.sizes()
-        ib = h.storage()[0]
+        ib, rb, _ = h.storage()
         # plain launches with CUDA events around every kernel on the library stream
         h.set_timing(True)
         h.begin(plan.w0, plan.alpha, plan.relaxation)
@@ -213,14 +216,15 @@ def run_gpu_arm(args):
         fb = fwd_bytes(sz["nnz_rows"], rows_nz, vb, ib, n_iter, n_iter)
         # chunk count is internal; it is small next to nnz (bounded by nnz/256 + n_spots)
         n_chunks_est = sz["nnz_rows"] // 2048 + sz["n_spots"]
-        bb = bwd_bytes(sz["nnz_rows"], rows_nz, n_chunks_est, vb, n_iter, n_iter)
+        bb = bwd_bytes(sz["nnz_rows"], rows_nz, n_chunks_est, vb, rb, n_iter, n_iter)
         f_ms, b_ms = kt["forward"][0], kt["backward"][0]
         fw = {"bound": "hbm", "achieved": fb / (f_ms * 1e-3) / 1e9 if f_ms else None, "peak": hbm,
               "unit": "GB/s", "kernel": "k_forward (fused Dx/Lx)", "index_bytes": ib, "launches": nf,
               "ms_total": f_ms,
               "bytes_per_launch": fb / max(1, 2 * n_iter)}
         bw = {"bound": "hbm", "achieved": bb / (b_ms * 1e-3) / 1e9 if b_ms else None, "peak": hbm,
-              "unit": "GB/s", "kernel": "k_backward (CSC chunks)", "launches": nb, "ms_total": b_ms,
+              "unit": "GB/s", "kernel": "k_backward (CSC chunks)", "row_index_bytes": rb, "launches": nb,
+              "ms_total": b_ms,
               "bytes_per_launch": bb / max(1, 2 * n_iter)}
         for r in (fw, bw):
             r["frac"] = r["achieved"] / hbm if r["achieved"] else None

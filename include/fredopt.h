@@ -57,11 +57,14 @@ extern "C" {
 #define FREDOPT_ROWS_ALL 0x000 /* every voxel row is streamed every pass (default) */
 #define FREDOPT_ROWS_ROI 0x100 /* only rows of voxels in some structure are streamed;
                                   dose/LETd of the other voxels are computed at the end */
-/* index width of the forward stream (or'ed into `format`): by default the
- * column indices are kept as 16-bit values when n_spots <= 65536 and the
- * fluence fits the forward kernel's shared memory (about 58000 spots on
- * GB300), which saves 2 bytes per nonzero and pass with identical results;
- * FREDOPT_INDEX32 keeps them 32-bit. */
+/* index widths of the streams (or'ed into `format`).  By default the
+ * forward stream keeps its column indices as 16-bit values when n_spots <=
+ * 65536 and the fluence fits the forward kernel's shared memory (about 58000
+ * spots on GB300), and the transposed product streams its row indices as
+ * 16-bit offsets from a base row per block of 128 nonzeros (blocks whose rows
+ * span 65536 or more keep 32-bit rows in a side table).  Each saves 2 bytes
+ * per nonzero and pass with identical results.  FREDOPT_INDEX32 keeps both
+ * streams 32-bit. */
 #define FREDOPT_INDEX32 0x200
 
 /* ---- constraint kinds (Fig. 2 half-spaces; the LETd limit LETd <= Lambda as the half-space (L - Lambda D) w <= 0) ----
@@ -326,8 +329,10 @@ int fredopt_get_sizes(fredopt_t h, int64_t* n_vox, int64_t* n_spots, int64_t* nn
 int fredopt_get_rows(fredopt_t h, int64_t* voxel, uint32_t* mask);
 
 /* Stored widths of the loaded plan: bytes per column index of the forward
- * stream (2 or 4, see FREDOPT_INDEX32) and per stored value (4 or 2). */
-int fredopt_get_storage(fredopt_t h, int* index_bytes, int* value_bytes);
+ * stream and per row index of the transposed product's stream (2 or 4 each,
+ * see FREDOPT_INDEX32), and per stored value (4 or 2).  NULL pointers are
+ * skipped. */
+int fredopt_get_storage(fredopt_t h, int* col_index_bytes, int* row_index_bytes, int* value_bytes);
 
 /* The CSC copy of the streamed rows: col_ptr int64[n_spots+1], row (index
  * into the streamed rows) int32[nnz_rows], D and L values float[nnz_rows]

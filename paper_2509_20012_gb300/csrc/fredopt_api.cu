@@ -81,6 +81,12 @@ struct fredopt_ctx {
   DBuf<double> mdd, mll, mdl;
   DBuf<int64_t> cp;
   DBuf<int32_t> crow;
+  // based 16-bit copy of crow for the transposed product (per 128-element
+  // block: base row in chdr, or an overflow slot of covf for wide blocks)
+  DBuf<uint16_t> crow16;
+  DBuf<int32_t> chdr, covf;
+  DBuf<unsigned int> cnw;
+  int64_t n_wide_blocks = 0;
   DBuf<uint8_t> DTv, LTv;
   DBuf<int64_t> warp_row_hot, warp_row_all, chunk_ptr;
   DBuf<int64_t> tile_row_hot;  // claimed tiles of the streamed rows (guided sizes)
@@ -370,6 +376,9 @@ FwdArgs fwd_args(fredopt_t h, bool hot) {
 BwdArgs bwd_args(fredopt_t h, const float2* coef) {
   BwdArgs b{};
   b.row = h->crow.p;
+  b.row16 = h->crow16.p;
+  b.hdr = h->chdr.p;
+  b.ovf = h->covf.p;
   b.Dv = h->DTv.p;
   b.Lv = h->LTv.p;
   b.chunk_ptr = h->chunk_ptr.p;
@@ -953,7 +962,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
 
   // ---- drop the previous plan
   h->rp.release(); h->col.release(); h->col16.release(); h->Dv.release(); h->Lv.release(); h->sD.release(); h->sL.release();
-  h->voxel.release(); h->mask.release(); h->cp.release(); h->crow.release(); h->DTv.release(); h->LTv.release();
+  h->voxel.release(); h->mask.release(); h->cp.release(); h->crow.release(); h->crow16.release(); h->chdr.release(); h->covf.release(); h->DTv.release(); h->LTv.release();
 
   // ---- FP32 CSR in device order (zero padded)
   DBuf<int32_t> col_d;
@@ -1060,6 +1069,26 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(cudaMemcpyAsync(&ferr, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ferr) return fail(h, FREDOPT_ERR_TIMEOUT, "a bounded device-side wait gave up (CSC transpose)");
+
+    // based 16-bit row indices for the transposed product (2 bytes less per
+    // nonzero and pass; crow stays for the sweep and inspection)
+    h->n_wide_blocks = 0;
+    if (!(format & FREDOPT_INDEX32)) {
+      const int64_t n_cblk = nh_alloc / 128;
+      CK(h->crow16.alloc(nh_alloc));
+      CK(h->chdr.alloc(n_cblk));
+      CK(h->cnw.ensure(2));
+      CK(cudaMemsetAsync(h->cnw.p, 0, 2 * sizeof(unsigned int), s));
+      launch_narrow_rows(h->crow.p, n_cblk, h->crow16.p, h->chdr.p, h->cnw.p, s);
+      CK(cudaGetLastError());
+      unsigned int n_wide = 0;
+      CK(cudaMemcpyAsync(&n_wide, h->cnw.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      CK(h->covf.alloc((size_t)std::max(1u, n_wide) * 128));
+      launch_narrow_rows_wide(h->crow.p, n_cblk, h->chdr.p, h->covf.p, h->cnw.p + 1, n_wide, s);
+      CK(cudaGetLastError());
+      h->n_wide_blocks = n_wide;
+    }
 
     // chunk schedule of the transposed product
     const int W3 = h->geo.bwd_warps;
@@ -1808,10 +1837,11 @@ int fredopt_get_sizes(fredopt_t h, int64_t* n_vox, int64_t* n_spots, int64_t* nn
   return FREDOPT_OK;
 }
 
-int fredopt_get_storage(fredopt_t h, int* index_bytes, int* val_bytes) {
+int fredopt_get_storage(fredopt_t h, int* col_index_bytes, int* row_index_bytes, int* val_bytes) {
   int rc = need_loaded(h);
   if (rc) return rc;
-  if (index_bytes) *index_bytes = h->col16.p ? 2 : 4;
+  if (col_index_bytes) *col_index_bytes = h->col16.p ? 2 : 4;
+  if (row_index_bytes) *row_index_bytes = h->crow16.p ? 2 : 4;
   if (val_bytes) *val_bytes = value_bytes(h->fmt);
   return FREDOPT_OK;
 }

@@ -6,7 +6,9 @@
 //         staged in shared memory; the int32 copy is then freed after the CSC
 //         build), Dv/Lv VT[nnz], sD/sL float[V] (16-bit only);
 //         col/D/L zero padded so whole 32*16-byte blocks past the end stay in bounds
-//   CSC   cp int64[n+1], row int32[nnz_hot] (index of a streamed row), DTv/LTv VT[nnz_hot]
+//   CSC   cp int64[n+1], row int32[nnz_hot] (index of a streamed row), DTv/LTv VT[nnz_hot];
+//         for the transposed product also row16 uint16[nnz_hot] offsets from
+//         per-128-element block bases hdr int32 (wide blocks in ovf)
 //   rows  voxel int64[V] (device row -> voxel), mask uint32[n_hot],
 //         FP64 moments |D_i|^2, |L_i|^2, <D_i,L_i> [n_hot]
 //   state w/g float[n], yw/yg/r/gam float2[n_hot], chunk_sum float[n_chunks],
@@ -108,6 +110,9 @@ struct FwdArgs {
 
 struct BwdArgs {
   const int32_t* row;
+  const uint16_t* row16;  // based 16-bit row offsets, or null (then row)
+  const int32_t* hdr;     // per 128-element block: base row, or -1 - overflow slot
+  const int32_t* ovf;     // 128 int32 rows per overflow slot
   const void* Dv;
   const void* Lv;
   const int64_t* chunk_ptr;   // [n_chunks + 1]
@@ -255,6 +260,13 @@ void launch_sweep_pos(const int64_t* cp, const int32_t* row, int32_t n, const in
 void launch_sweep_update(const Geometry& g, int fmt, const SweepArgs& a, cudaStream_t s);
 void launch_sweep_finish(const Geometry& g, int n, const float* x, float* out, int in_solve, DevState* st,
                          LogEntry* log, cudaStream_t s);
+// Based 16-bit CSC row indices over n_blk blocks of 128 elements (pass 1:
+// bases, offsets, wide blocks marked and counted in *n_wide; pass 2: overflow
+// slots of the n_wide marked blocks, *slot zeroed before).
+void launch_narrow_rows(const int32_t* row, int64_t n_blk, uint16_t* row16, int32_t* hdr, unsigned int* n_wide,
+                        cudaStream_t s);
+void launch_narrow_rows_wide(const int32_t* row, int64_t n_blk, int32_t* hdr, int32_t* ovf, unsigned int* slot,
+                             unsigned int n_wide, cudaStream_t s);
 // out[i] = in[i] for i < n (in[i] < 65536), n a multiple of 4.
 void launch_narrow_idx(const int32_t* in, uint16_t* out, int64_t n, cudaStream_t s);
 // One CTA in the bounded wait of the bulk copies (spins <= 0: their bound).

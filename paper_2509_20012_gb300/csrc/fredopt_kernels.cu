@@ -58,13 +58,32 @@ constexpr int kBwdUnroll = FO_BWD_UNROLL;
 #ifndef FO_UNROLL16
 #define FO_UNROLL16 2
 #endif
+#ifndef FO_BWD_UNROLL16
+#define FO_BWD_UNROLL16 FO_UNROLL16
+#endif
+#ifndef FO_BWD_PP
+#define FO_BWD_PP 0
+#endif
 constexpr int kFwdUnroll16 = FO_UNROLL16;
-constexpr int kBwdUnroll16 = FO_UNROLL16;
+constexpr int kBwdUnroll16 = FO_BWD_UNROLL16;
+constexpr bool kBwdPingPong = FO_BWD_PP != 0;
 constexpr int kPrefetchUnits = FO_PREFETCH_UNITS;
 constexpr int kBwdThreads = 256;
 constexpr int kRowThreads = 256;
 constexpr int kColThreads = 256;
 constexpr int kMbarSpins = FREDOPT_WAIT_POLLS;
+// transposed product: lane-strided elements (one gather instruction reads
+// the coefficients of 32 consecutive CSC elements) for FP32 values; 16-bit
+// values keep 4 consecutive elements per lane (8-byte loads), which measured
+// faster there
+#ifndef FO_BWD_TR
+#define FO_BWD_TR 1
+#endif
+#ifndef FO_BWD_TR16
+#define FO_BWD_TR16 0
+#endif
+template <typename VT>
+constexpr bool kBwdStrided = sizeof(VT) == 4 ? FO_BWD_TR != 0 : FO_BWD_TR16 != 0;
 
 // ------------------------------------------------------------------ helpers
 
@@ -255,6 +274,16 @@ template <typename VT>
 struct Blk {
   int4 c0;      // 4 indices
   uint4 a, b;   // values of the two streams
+  int hb;       // block header of based 16-bit indices (see BlockBase)
+};
+
+// Based 16-bit indices: the stream is cut into aligned blocks of 128
+// elements; block k holds uint16 offsets from hdr[k] >= 0, or, when its
+// indices span 65536 or more, hdr[k] = -1 - j and its 128 int32 indices are
+// ovf[128 j .. 128 j + 127].
+struct BlockBase {
+  const int32_t* hdr;
+  const int32_t* ovf;
 };
 
 template <bool S>
@@ -296,6 +325,33 @@ __device__ __forceinline__ void load_blk(Blk<VT>& k, const IT* idx, const VT* Av
   k.b = ld_vals<S>(Bv + p);
 }
 
+// Lane-strided block: elements p, p + 32, p + 64, p + 96 (p = block start +
+// lane), packed into the same registers as load_blk's 4 consecutive ones.
+template <bool S, typename T>
+__device__ __forceinline__ T ld1(const T* p) {
+  if (S) return __ldcs(p);
+  return __ldg(p);
+}
+template <bool S, typename T>
+__device__ __forceinline__ uint4 ld_strided(const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    const unsigned* q = reinterpret_cast<const unsigned*>(p);
+    return make_uint4(ld1<S>(q), ld1<S>(q + 32), ld1<S>(q + 64), ld1<S>(q + 96));
+  } else {
+    const unsigned short* q = reinterpret_cast<const unsigned short*>(p);
+    const uint32_t e0 = ld1<S>(q), e1 = ld1<S>(q + 32), e2 = ld1<S>(q + 64), e3 = ld1<S>(q + 96);
+    return make_uint4(e0 | (e1 << 16), e2 | (e3 << 16), 0u, 0u);
+  }
+}
+template <typename VT, bool S, bool USE_A, typename IT>
+__device__ __forceinline__ void load_blk_strided(Blk<VT>& k, const IT* idx, const VT* Av, const VT* Bv,
+                                                 int64_t p) {
+  const uint4 c = ld_strided<S>(idx + p);
+  k.c0 = make_int4((int)c.x, (int)c.y, (int)c.z, (int)c.w);
+  if (USE_A) k.a = ld_strided<S>(Av + p);
+  k.b = ld_strided<S>(Bv + p);
+}
+
 // Streams the elements [ptr[r0], ptr[r1]) of one warp as consecutive blocks
 // of 32*V elements (lane l holds elements l*V .. l*V+V-1 of a block; every
 // load is 16 bytes; the next unit of U blocks is in flight while the
@@ -305,23 +361,31 @@ __device__ __forceinline__ void load_blk(Blk<VT>& k, const IT* idx, const VT* Av
 // butterfly; lane (r - base) keeps it; every 32 segments (and at the end)
 // flush(base, count, mine_A, mine_B) runs with lane j < count owning segment
 // base + j.  Deterministic: the split depends only on ptr, r0, r1.  The index
-// stream is int32 or uint16 (IT); the sums do not depend on its width.
+// stream is int32 or uint16 (IT), the latter plain or BASED on per-block
+// headers (bb); the sums do not depend on the encoding.  TR: lane l holds
+// elements l, l + 32, l + 64, l + 96 of a block instead, so that one gather
+// instruction of the warp reads 32 consecutive elements' indices (fewer L1
+// sectors per gather when consecutive indices are close); the loads are
+// then 4 or 2 bytes per lane, still coalesced.
 // The arrays must be readable (zero padded) up to
 // round_up(ptr[r1], 32*V) + U*32*V elements (a prefetch starts below ptr[r1]
 // and covers U*32*V elements, within the same bound).
-template <typename VT, typename Acc, bool S, bool USE_A, int U, typename IT, class Gather, class Flush,
-          int PF = kPrefetchUnits, bool PP = false>
+template <typename VT, typename Acc, bool S, bool USE_A, int U, bool BASED = false, bool TR = false,
+          typename IT, class Gather, class Flush, int PF = kPrefetchUnits, bool PP = false>
 __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
                                                 const VT* __restrict__ Av, const VT* __restrict__ Bv,
                                                 const int64_t* __restrict__ ptr, int64_t r0, int64_t r1,
-                                                int lane, Gather gather, Flush flush) {
+                                                int lane, Gather gather, Flush flush,
+                                                BlockBase bbase = BlockBase{nullptr, nullptr}) {
   constexpr int V = VecOf<VT>::V;
   constexpr int BLK = 32 * V;
   constexpr int UB = U * BLK;
+  static_assert(!BASED || (BLK == 128 && sizeof(IT) == 2), "based indices: 16-bit, 128-element blocks");
   if (r0 >= r1) return;
   // 32-bit offsets from the block-aligned start of the warp's range (a
   // warp's range is far below 2^31 elements)
   const int64_t start = ptr[r0] & ~(int64_t)(BLK - 1);
+  const int32_t* __restrict__ hdr = BASED ? bbase.hdr + start / BLK : nullptr;
   idx += start;
   if (USE_A) Av += start;
   Bv += start;
@@ -339,10 +403,27 @@ __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
     for (int u = 0; u < U; ++u) {
       if (done) return;
       const int bb = b + u * BLK;
-      const int e0 = bb + lane * V;
+      const int e0 = bb + (TR ? lane : lane * V);
+      constexpr int QS = TR ? 32 : 1;  // element stride between a lane's values
       int cs[V];
       float av[V], bv[V];
       unpack_idx(IT(), unit[u].c0, cs);
+      if (BASED) {
+        const int hb = unit[u].hb;
+        if (hb >= 0) {
+#pragma unroll
+          for (int q = 0; q < V; ++q) cs[q] += hb;
+        } else {  // wide block: its int32 indices from the overflow table
+          const int32_t* ov = bbase.ovf + (int64_t)(-1 - hb) * BLK;
+          if (TR) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) cs[q] = __ldg(ov + q * 32 + lane);
+          } else {
+            const int4 w = __ldg(reinterpret_cast<const int4*>(ov) + lane);
+            cs[0] = w.x; cs[1] = w.y; cs[2] = w.z; cs[3] = w.w;
+          }
+        }
+      }
       if (USE_A) unpack(VT(), unit[u].a, av);
       unpack(VT(), unit[u].b, bv);
       float2 gv[V];
@@ -353,7 +434,7 @@ __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
         const int hi = e_cur < bb + BLK ? e_cur : bb + BLK;
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-          const int e = e0 + q;
+          const int e = e0 + q * QS;
           if (e >= lo && e < hi) {
             if (USE_A) sA = acc_fma(av[q], gv[q].x, sA);
             sB = acc_fma(bv[q], gv[q].y, sB);
@@ -389,7 +470,11 @@ __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
   auto load_unit = [&](Blk<VT>* unit, int b) {
     prefetch_unit(b + PF * UB);
 #pragma unroll
-    for (int u = 0; u < U; ++u) load_blk<VT, S, USE_A, IT>(unit[u], idx, Av, Bv, b + u * BLK + lane * V);
+    for (int u = 0; u < U; ++u) {
+      if (TR) load_blk_strided<VT, S, USE_A, IT>(unit[u], idx, Av, Bv, b + u * BLK + lane);
+      else load_blk<VT, S, USE_A, IT>(unit[u], idx, Av, Bv, b + u * BLK + lane * V);
+      if (BASED) unit[u].hb = __ldg(hdr + (b + u * BLK) / BLK);
+    }
   };
 
   int b = 0;
@@ -561,7 +646,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(Fwd
 
 // Chunk sums of the transposed product: chunk c = nonzeros [chunk_ptr[c],
 // chunk_ptr[c+1]) of one column; sum_i D_ij coef_i.x + L_ij coef_i.y.
-template <typename VT, bool S, bool UD>
+// NB: row indices as based 16-bit offsets (BwdArgs.row16/hdr/ovf).
+template <typename VT, bool S, bool UD, bool NB>
 __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(BwdArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -582,8 +668,15 @@ __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(Bwd
   };
   int job = a.sched ? claim() : warp;
   while (job < a.n_warps) {
-    stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16)>(
-        a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush);
+    if (NB)
+      stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16), true, kBwdStrided<VT>,
+                      uint16_t, decltype(gather), decltype(flush), kPrefetchUnits, kBwdPingPong>(
+          a.row16, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush,
+          BlockBase{a.hdr, a.ovf});
+    else
+      stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16), false, kBwdStrided<VT>,
+                      int32_t, decltype(gather), decltype(flush), kPrefetchUnits, kBwdPingPong>(
+          a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush);
     if (!a.sched) break;
     job = claim();
   }
@@ -1350,15 +1443,20 @@ void launch_forward(const Geometry& g, int fmt, int epi, bool stream_hint, const
   else fwd_dispatch_epi<float>(g, epi, xs, stream_hint, a, t, s);
 }
 
+template <typename VT, bool NB>
+static void bwd_dispatch_nb(const Geometry& g, bool st, bool ud, const BwdArgs& a, cudaStream_t s) {
+  if (st) {
+    if (ud) k_backward<VT, true, true, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+    else k_backward<VT, true, false, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+  } else {
+    if (ud) k_backward<VT, false, true, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+    else k_backward<VT, false, false, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+  }
+}
 template <typename VT>
 static void bwd_dispatch(const Geometry& g, bool st, bool ud, const BwdArgs& a, cudaStream_t s) {
-  if (st) {
-    if (ud) k_backward<VT, true, true><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
-    else k_backward<VT, true, false><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
-  } else {
-    if (ud) k_backward<VT, false, true><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
-    else k_backward<VT, false, false><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
-  }
+  if (a.row16) bwd_dispatch_nb<VT, true>(g, st, ud, a, s);
+  else bwd_dispatch_nb<VT, false>(g, st, ud, a, s);
 }
 
 void launch_backward(const Geometry& g, int fmt, bool stream_hint, bool use_D, const BwdArgs& a,
@@ -1588,7 +1686,7 @@ int init_kernels(Geometry* g, int device) {
   g->fwd_blocks = g->n_sms * (FO_FWD_XS ? 1 : 1024 / kFwdThreads);
   g->fwd_warps = g->fwd_blocks * (kFwdThreads / 32);
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<float, true, true>, kBwdThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<float, true, true, false>, kBwdThreads, 0);
   if (occ < 1) occ = 1;
   g->bwd_threads = kBwdThreads;
   g->bwd_blocks = g->n_sms * occ;
@@ -1757,6 +1855,69 @@ void launch_narrow_idx(const int32_t* in, uint16_t* out, int64_t n, cudaStream_t
   if (n4 == 0) return;
   const unsigned grid = (unsigned)std::min<int64_t>((n4 + 255) / 256, 152 * 8);
   k_narrow_idx<<<grid, 256, 0, s>>>(reinterpret_cast<const int4*>(in), reinterpret_cast<uint2*>(out), n4);
+}
+
+// Based 16-bit row indices of the CSC (see BlockBase): one warp per block of
+// 128 elements.  Pass 1 writes the block's base and offsets when its rows
+// span less than 65536, else marks it -1 and counts it; pass 2 gives every
+// marked block an overflow slot and copies its 128 int32 rows there.
+__global__ void __launch_bounds__(256) k_narrow_rows(const int32_t* __restrict__ row, int64_t n_blk,
+                                                     uint16_t* __restrict__ row16, int32_t* __restrict__ hdr,
+                                                     unsigned int* n_wide) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_blk; k += wstride) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(row + k * 128) + lane);
+    int lo = min(min(v.x, v.y), min(v.z, v.w)), hi = max(max(v.x, v.y), max(v.z, v.w));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+      hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    if ((int64_t)hi - (int64_t)lo < 65536) {
+      reinterpret_cast<uint2*>(row16 + k * 128)[lane] =
+          make_uint2((uint32_t)(v.x - lo) | ((uint32_t)(v.y - lo) << 16),
+                     (uint32_t)(v.z - lo) | ((uint32_t)(v.w - lo) << 16));
+      if (lane == 0) hdr[k] = lo;
+    } else {
+      reinterpret_cast<uint2*>(row16 + k * 128)[lane] = make_uint2(0u, 0u);
+      if (lane == 0) {
+        hdr[k] = -1;
+        atomicAdd(n_wide, 1u);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_narrow_rows_wide(const int32_t* __restrict__ row, int64_t n_blk,
+                                                          int32_t* __restrict__ hdr, int32_t* __restrict__ ovf,
+                                                          unsigned int* slot, unsigned int n_wide) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_blk; k += wstride) {
+    if (hdr[k] != -1) continue;
+    unsigned j = 0;
+    if (lane == 0) j = atomicAdd(slot, 1u);
+    j = __shfl_sync(kFull, j, 0);
+    if (j >= n_wide) continue;  // cannot happen: pass 1 counted every marked block
+    reinterpret_cast<int4*>(ovf + (int64_t)j * 128)[lane] = __ldg(reinterpret_cast<const int4*>(row + k * 128) + lane);
+    __syncwarp();
+    if (lane == 0) hdr[k] = -1 - (int32_t)j;
+  }
+}
+
+void launch_narrow_rows(const int32_t* row, int64_t n_blk, uint16_t* row16, int32_t* hdr, unsigned int* n_wide,
+                        cudaStream_t s) {
+  if (n_blk == 0) return;
+  const unsigned grid = (unsigned)std::min<int64_t>((n_blk + 7) / 8, 152 * 8);
+  k_narrow_rows<<<grid, 256, 0, s>>>(row, n_blk, row16, hdr, n_wide);
+}
+
+void launch_narrow_rows_wide(const int32_t* row, int64_t n_blk, int32_t* hdr, int32_t* ovf, unsigned int* slot,
+                             unsigned int n_wide, cudaStream_t s) {
+  if (n_blk == 0 || n_wide == 0) return;
+  const unsigned grid = (unsigned)std::min<int64_t>((n_blk + 7) / 8, 152 * 8);
+  k_narrow_rows_wide<<<grid, 256, 0, s>>>(row, n_blk, hdr, ovf, slot, n_wide);
 }
 
 // Failure detection without a fault: one CTA polls an mbarrier phase with the

@@ -21,7 +21,7 @@ OK = 0
 DEVICE_PTR = 0x1
 FORMATS = {"fp32": 0, "bf16": 1, "fp16": 2}
 ROWS = {"all": 0x000, "roi": 0x100}
-INDEX32 = 0x200  # keep 32-bit column indices in the forward stream
+INDEX32 = 0x200  # keep 32-bit indices in the forward and transposed streams
 KINDS = {"DOSE_MIN": 0, "DOSE_MAX": 1, "CDL_MIN": 2, "CDL_MAX": 3, "LETD_MIN": 4, "LETD_MAX": 5}
 QUANTITIES = {"DOSE": 0, "CDL": 1, "LETD": 2}  # LETD: volume statistics only
 VOLUME_MAX_REQUESTS, VOLUME_MAX_BINS, VOLUME_MAX_FRACS = 64, 16384, 64
@@ -156,7 +156,7 @@ _SIGS = {
     "fredopt_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fredopt_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fredopt_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
-    "fredopt_get_storage": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "fredopt_get_storage": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3),
     "fredopt_check_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "fredopt_footprint_bytes": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int]),
     "fredopt_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64,
@@ -320,10 +320,11 @@ class Handle:
         self.set_objective(plan.objective)
 
     def storage(self):
-        """(index bytes, value bytes) of the loaded plan's forward stream."""
-        ib, vb = ctypes.c_int(), ctypes.c_int()
-        self._check(self.lib.fredopt_get_storage(self.h, ctypes.byref(ib), ctypes.byref(vb)))
-        return ib.value, vb.value
+        """(column index bytes of the forward stream, row index bytes of the
+        transposed product's stream, value bytes) of the loaded plan."""
+        ib, rb, vb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.fredopt_get_storage(self.h, ctypes.byref(ib), ctypes.byref(rb), ctypes.byref(vb)))
+        return ib.value, rb.value, vb.value
 
     def sizes(self):
         v = [ctypes.c_int64() for _ in range(5)]

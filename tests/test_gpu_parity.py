@@ -335,8 +335,9 @@ def test_claimed_tiles_equal_static_tiles(lib, tiny, rows):
 @pytest.mark.parametrize("fmt", ["fp32", "bf16"])
 @pytest.mark.parametrize("rows", ["all", "roi"])
 def test_index16_equals_index32(lib, tiny, fmt, rows):
-    """16-bit column indices (the default when the spots fit) and 32-bit ones
-    stream the same elements in the same order: forward products, sweeps,
+    """16-bit indices (forward columns when the spots fit; transposed-product
+    rows as offsets from per-block bases) and 32-bit ones stream the same
+    elements in the same order: forward and transposed products, sweeps,
     iterates, logs and final outputs are bit-identical."""
     pl, P, R = tiny
     x = np.random.default_rng(11).uniform(0.0, 2.0, pl.n_spots).astype(np.float32)
@@ -344,15 +345,17 @@ def test_index16_equals_index32(lib, tiny, fmt, rows):
     for index32 in (False, True):
         with lib.Handle(0) as h:
             h.load_plan(pl, fmt=fmt, rows=rows, index32=index32)
-            assert h.storage() == (4 if index32 else 2, 4 if fmt == "fp32" else 2)
+            assert h.storage() == (4, 4, 4 if fmt == "fp32" else 2) if index32 else \
+                h.storage() == (2, 2, 4 if fmt == "fp32" else 2)
             dose, lw = h.forward(x)
+            u = h.backward(dose, lw)
             sw = h.sweep_step(x, 16)
             w, d, l, rep = h.superiorize(pl.w0, 15, pl.alpha, pl.relaxation)
-            out.append((dose, lw, sw, w, d, l, h.get_log()))
+            out.append((dose, lw, u, sw, w, d, l, h.get_log()))
     a, b = out
-    for u, v in zip(a[:6], b[:6]):
+    for u, v in zip(a[:7], b[:7]):
         np.testing.assert_array_equal(u, v)
-    assert a[6] == b[6]
+    assert a[7] == b[7]
 
 
 @pytest.mark.parametrize("n_cols,index_bytes", [(1, 2), (58000, 2), (60000, 4), (70000, 4)])
@@ -374,6 +377,32 @@ def test_index_width_by_spot_count(lib, n_cols, index_bytes):
         l_ref = L[s:e].astype(np.float64) @ x64[col[s:e]]
         assert abs(dose[i] - d_ref) <= 1e-5 * abs(d_ref) + 1e-30
         assert abs(lw[i] - l_ref) <= 1e-5 * abs(l_ref) + 1e-30
+
+
+@pytest.mark.parametrize("n_rows,n_cols,density", [(300000, 20, 0.0004), (200000, 40, 0.01), (70000, 3, 0.9)])
+def test_based_row_indices_wide_blocks(lib, n_rows, n_cols, density):
+    """Transposed product with based 16-bit row indices on columns whose
+    blocks of 128 nonzeros span 65536 rows or more (sparse columns over
+    300000 rows; blocks across column boundaries): bit-identical to the
+    32-bit stream and within 1e-5 of the FP64 column sums."""
+    rp, col, D, L = phantom.random_csr(n_rows, n_cols, density, seed=n_rows + n_cols, empty_rows=11)
+    mask = np.ones(n_rows, np.uint32)
+    rng = np.random.default_rng(3)
+    aD = rng.normal(size=n_rows).astype(np.float32)
+    aL = rng.normal(size=n_rows).astype(np.float32)
+    out = []
+    for index32 in (False, True):
+        with lib.Handle(0) as h:
+            h.load_influence(rp, col, D, L, mask, n_cols, index32=index32)
+            assert h.storage()[1] == (4 if index32 else 2)
+            out.append(h.backward(aD, aL))
+    np.testing.assert_array_equal(out[0], out[1])
+    rows = np.repeat(np.arange(n_rows), np.diff(rp))
+    tD = D.astype(np.float64) * aD[rows]
+    tL = L.astype(np.float64) * aL[rows]
+    ref = np.bincount(col, weights=tD + tL, minlength=n_cols)
+    bound = np.bincount(col, weights=np.abs(tD) + np.abs(tL), minlength=n_cols)
+    assert np.all(np.abs(out[0] - ref) <= 1e-5 * bound + 1e-30)
 
 
 def test_checkpoint_resume_bit_exact(lib, tiny):
