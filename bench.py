@@ -125,6 +125,9 @@ class ClockSampler:
 # traffic grows with the nonzeros, so it is scaled to the full plan.  A
 # stream without a capture reports null.
 FWD_TRAFFIC_PER_NNZ = {("fp32", 4): 12.48, ("fp32", 2): 10.17}
+# the same for the transposed product (average of its gradient and projection
+# launches), keyed by (storage, row index bytes)
+BWD_TRAFFIC_PER_NNZ = {("fp32", 2): 8.26}
 
 
 def fwd_bytes(nnz, rows, vb, ib, n_launch_obj, n_launch_bc):
@@ -230,7 +233,8 @@ def run_gpu_arm(args):
             r["frac"] = r["achieved"] / hbm if r["achieved"] else None
         t = FWD_TRAFFIC_PER_NNZ.get((fmt, ib))
         fw["traffic"] = t * sz["nnz_rows"] if t else None
-        bw["traffic"] = None
+        t = BWD_TRAFFIC_PER_NNZ.get((fmt, rb))
+        bw["traffic"] = t * sz["nnz_rows"] if t else None
         return dict(ms=ms, kt=kt, launches=launches, clocks=clocks, rep=rep, sizes=sz, t_load=t_load,
                     fwd=fw, bwd=bw, w=w, dose=dose, letd=letd)
 
@@ -349,7 +353,8 @@ def run_gpu_arm(args):
             line["batching"] = batching
         if prec:
             line["precision"] = {"note": ("D and L stored in 16 bits with power-of-two FP32 row scales, "
-                                          "int32 indices, FP32 accumulation, FP64 norms and final check; "
+                                          "16-bit indices (bit-identical to int32 ones), FP32 accumulation, FP64 norms and final "
+                                          "check; "
                                           "errors of the outputs at each run's final w against the FP64 "
                                           "product of the FP32 inputs"), **prec}
         if roi is not None:
