@@ -38,7 +38,9 @@ extern "C" {
 #define FREDOPT_OK 0
 #define FREDOPT_ERR_INVALID_ARG (-1) /* bad scalar argument or null pointer */
 #define FREDOPT_ERR_SHAPE (-2)       /* sizes inconsistent or out of range */
-#define FREDOPT_ERR_PATTERN (-3)     /* CSR not monotone, column out of range or unsorted */
+#define FREDOPT_ERR_PATTERN (-3)     /* CSR not monotone, column out of range or unsorted; in a
+                                        library built with FO_CHECKED=1 also: a streaming kernel
+                                        found a tile range or index out of bounds */
 #define FREDOPT_ERR_NONFINITE (-4)   /* NaN or Inf in an input */
 #define FREDOPT_ERR_NOT_LOADED (-5)  /* call needs a loaded plan / constraints / begun solve */
 #define FREDOPT_ERR_OOM (-6)         /* device allocation failed */

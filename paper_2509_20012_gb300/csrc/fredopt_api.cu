@@ -354,6 +354,7 @@ FwdArgs fwd_args(fredopt_t h, bool hot) {
   a.rp = h->rp.p;
   a.col = h->col.p;
   a.col16 = h->col16.p;
+  a.n_elems = (int64_t)(h->col16.p ? h->col16.n : h->col.n);
   a.Dv = h->Dv.p;
   a.Lv = h->Lv.p;
   a.sD = h->fmt ? h->sD.p : nullptr;
@@ -375,6 +376,10 @@ FwdArgs fwd_args(fredopt_t h, bool hot) {
 
 BwdArgs bwd_args(fredopt_t h, const float2* coef) {
   BwdArgs b{};
+  b.st = h->st.p;
+  b.n_rows = h->n_hot;
+  b.n_elems = (int64_t)h->crow.n;
+  b.n_ovf = (int32_t)h->n_wide_blocks;
   b.row = h->crow.p;
   b.row16 = h->crow16.p;
   b.hdr = h->chdr.p;
@@ -702,6 +707,7 @@ int check_sticky(fredopt_t h) {
     // a pass that gave up may have left its tile counters set
     if (h->fsched.p) cudaMemset(h->fsched.p, 0, 2 * sizeof(unsigned int));
     if (h->bsched.p) cudaMemset(h->bsched.p, 0, 2 * sizeof(unsigned int));
+    if (err & 2) return fail(h, FREDOPT_ERR_PATTERN, "checked build: an index or tile range out of bounds");
     return fail(h, FREDOPT_ERR_TIMEOUT, "a bounded device-side wait gave up (bulk copy)");
   }
   return FREDOPT_OK;

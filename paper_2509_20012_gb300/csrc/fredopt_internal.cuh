@@ -61,7 +61,7 @@ struct DevState {
   long long k, s, accepted_total;
   int accepted;       // accepted steps in the current iteration
   int reductions, max_trials, norm, grad_normalize, log_cap;
-  int err;            // bit 0: bulk-copy wait timed out
+  int err;            // bit 0: bulk-copy wait timed out; bit 1: index out of range (FO_CHECKED builds)
   unsigned int done;  // last-block counter of the column finish
   int pad;
   double sweep_nv, sweep_mx;  // block-iterative sweep: violated rows and largest violation
@@ -81,6 +81,7 @@ enum FwdEpi { EPI_STORE = 0, EPI_OBJ = 1, EPI_BC = 2, EPI_FINAL = 3 };
 enum ColMode { COL_OUT = 0, COL_GRAD = 1, COL_PROJ = 2 };
 
 struct FwdArgs {
+  int64_t n_elems;        // allocated elements of the streamed arrays
   const int64_t* rp;
   const int32_t* col;     // column indices, or null when col16 is set
   const uint16_t* col16;  // 16-bit column indices (x staged in shared memory only)
@@ -109,6 +110,10 @@ struct FwdArgs {
 };
 
 struct BwdArgs {
+  DevState* st;
+  int64_t n_rows;         // streamed rows (range of the row indices)
+  int64_t n_elems;        // allocated elements of the streamed arrays
+  int32_t n_ovf;          // overflow slots of wide blocks
   const int32_t* row;
   const uint16_t* row16;  // based 16-bit row offsets, or null (then row)
   const int32_t* hdr;     // per 128-element block: base row, or -1 - overflow slot

@@ -295,6 +295,21 @@ struct Blk {
 struct BlockBase {
   const int32_t* hdr;
   const int32_t* ovf;
+  int32_t n_ovf;
+};
+
+// Checked builds (FO_CHECKED=1, a debug aid in place of a memory checker):
+// the streaming kernels check every tile's element range against the
+// allocated length, every gathered index against its table and every
+// overflow slot, record a failure in bit 1 of the error word (reported as
+// FREDOPT_ERR_PATTERN) and skip the access.  Results are otherwise
+// bit-identical to the default build.
+#ifndef FO_CHECKED
+#define FO_CHECKED 0
+#endif
+struct SegCheck {
+  int64_t n_elems;
+  int* err;
 };
 
 template <bool S>
@@ -404,12 +419,22 @@ __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
                                                 const VT* __restrict__ Av, const VT* __restrict__ Bv,
                                                 const int64_t* __restrict__ ptr, int64_t r0, int64_t r1,
                                                 int lane, Gather gather, Flush flush,
-                                                BlockBase bbase = BlockBase{nullptr, nullptr}) {
+                                                BlockBase bbase = BlockBase{nullptr, nullptr, 0},
+                                                SegCheck chk = SegCheck{0, nullptr}) {
   constexpr int V = VecOf<VT>::V;
   constexpr int BLK = 32 * V;
   constexpr int UB = U * BLK;
   static_assert(!BASED || (BLK == 128 && sizeof(IT) == 2), "based indices: 16-bit, 128-element blocks");
   if (r0 >= r1) return;
+#if FO_CHECKED
+  if (chk.err) {
+    const int64_t p0 = ptr[r0], p1 = ptr[r1];
+    if (p0 < 0 || p1 < p0 || (p1 + BLK - 1) / BLK * BLK + UB > chk.n_elems) {
+      if (lane == 0) atomicOr(chk.err, 2);
+      return;
+    }
+  }
+#endif
   // 32-bit offsets from the block-aligned start of the warp's range (a
   // warp's range is far below 2^31 elements)
   const int64_t start = ptr[r0] & ~(int64_t)(BLK - 1);
@@ -440,7 +465,14 @@ __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
 #pragma unroll
           for (int q = 0; q < V; ++q) cs[q] += hb;
         } else {  // wide block: its int32 indices from the overflow table
-          const int32_t* ov = bbase.ovf + (int64_t)(-1 - hb) * BLK;
+          int slot = -1 - hb;
+#if FO_CHECKED
+          if (slot >= bbase.n_ovf) {
+            if (chk.err) atomicOr(chk.err, 2);
+            slot = 0;
+          }
+#endif
+          const int32_t* ov = bbase.ovf + (int64_t)slot * BLK;
           if (LM == 1) {
 #pragma unroll
             for (int q = 0; q < V; ++q) cs[q] = __ldg(ov + q * 32 + lane);
@@ -608,6 +640,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(Fwd
   const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
   double acc0 = 0.0, acc1 = 0.0;  // per-lane partials of the epilogue reductions
   auto gather = [&](int c) {
+#if FO_CHECKED
+    if ((unsigned)c >= (unsigned)a.n_x) {
+      atomicOr(&a.st->err, 2);
+      c = 0;
+    }
+#endif
     const float v = x[c];
     return make_float2(v, v);
   };
@@ -649,8 +687,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(Fwd
     const int64_t r0 = a.warp_row[2 * job], r1 = a.warp_row[2 * job + 1];
     acc0 = 0.0;
     acc1 = 0.0;
-    stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : kFwdUnroll16)>(fwd_col<IT>(a), Dv, Lv, a.rp,
-                                                                            r0, r1, lane, gather, flush);
+    stream_segments<VT, Acc, S, true, (sizeof(VT) == 4 ? kFwdUnroll : kFwdUnroll16)>(
+        fwd_col<IT>(a), Dv, Lv, a.rp, r0, r1, lane, gather, flush, BlockBase{nullptr, nullptr, 0},
+        SegCheck{a.n_elems, FO_CHECKED ? &a.st->err : nullptr});
     if (EPI == EPI_OBJ || EPI == EPI_BC) {  // partials per tile, summed later in tile order
       const double s0 = warp_sum(acc0), s1 = warp_sum(acc1);
       if (lane == 0) {
@@ -685,7 +724,15 @@ __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(Bwd
   const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
   const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
   const float2* __restrict__ cf = a.coef;
-  auto gather = [&](int r) { return __ldg(&cf[r]); };
+  auto gather = [&](int r) {
+#if FO_CHECKED
+    if ((uint64_t)(int64_t)r >= (uint64_t)a.n_rows) {
+      atomicOr(&a.st->err, 2);
+      r = 0;
+    }
+#endif
+    return __ldg(&cf[r]);
+  };
   float* out = a.chunk_sum;
   auto flush = [&](int64_t base, int cnt, float mA, float mB) {
     if (lane < cnt) out[base + lane] = UD ? mA + mB : mB;
@@ -703,11 +750,12 @@ __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(Bwd
       stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16), true, kBwdLaneMap<VT>,
                       uint16_t, decltype(gather), decltype(flush), kPrefetchUnits, kBwdPingPong>(
           a.row16, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush,
-          BlockBase{a.hdr, a.ovf});
+          BlockBase{a.hdr, a.ovf, a.n_ovf}, SegCheck{a.n_elems, FO_CHECKED ? &a.st->err : nullptr});
     else
       stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16), false, kBwdLaneMap<VT>,
                       int32_t, decltype(gather), decltype(flush), kPrefetchUnits, kBwdPingPong>(
-          a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush);
+          a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush,
+          BlockBase{nullptr, nullptr, 0}, SegCheck{a.n_elems, FO_CHECKED ? &a.st->err : nullptr});
     if (!a.sched) break;
     job = claim();
   }
