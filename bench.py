@@ -328,8 +328,9 @@ def run_gpu_arm(args):
             "config": {"workload": WORKLOAD, "rows": "all voxel rows streamed every pass",
                        "n_vox": main["sizes"]["n_vox"], "n_spots": main["sizes"]["n_spots"],
                        "nnz_per_matrix": main["sizes"]["nnz"], "storage": "fp32",
-                       "l2": "inputs larger than L2 (each pass streams %.1f GB)" % (
-                           main["sizes"]["nnz"] * 12 / 1e9),
+                       "l2": "inputs larger than L2 (each forward pass streams %.1f GB, each "
+                             "transposed pass %.1f GB on average)" % (
+                           main["fwd"]["bytes_per_launch"] / 1e9, main["bwd"]["bytes_per_launch"] / 1e9),
                        "parallelism": f"replicas{ws}", "generate_s": round(t_gen, 2),
                        "load_s": round(main["t_load"], 3)},
             "roofline": {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")} | {
