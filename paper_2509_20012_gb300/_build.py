@@ -1,7 +1,10 @@
 """In-tree build of libfredopt.so for sm_103a (nvcc; no cmake).
 
-The two translation units compile in parallel, then link into
+The translation units (kernels, C ABI, server, no-allocation product, volume
+statistics) compile in parallel, then link into
 paper_2509_20012_gb300/libfredopt.so with the CUDA runtime linked statically.
+`defines` builds variants elsewhere, e.g. the bounds-checked FO_CHECKED=1
+library that tests/test_gpu_checked.py loads.
 Rebuilds only when a source or header is newer than the library.
 """
 from __future__ import annotations
