@@ -242,8 +242,9 @@ int64_t fredopt_footprint_bytes(int64_t n_vox, int32_t n_spots, int64_t nnz, int
   const int fmt = format & 0xff;
   const int64_t vb = fmt == FREDOPT_FP32 ? 4 : 2;
   const int64_t na = ((nnz + 255) & ~255LL) + fo::kPadElems;
-  // peak of the load: FP32 upload + gathered copy, then CSR + CSC + tables
-  const int64_t load_peak = 2 * na * 12;
+  // peaks of the load: FP32 upload + gathered copy; then, while the 16-bit
+  // index copies are made, CSR + CSC (int32 indices) + both 16-bit copies
+  const int64_t load_peak = std::max(2 * na * 12, na * (2 * (4 + 2 * vb) + 4));
   const int64_t resident = na * (4 + 2 * vb) * 2 + (fmt ? na * 8 : 0);
   const int64_t per_row = n_vox * (8 + 8 + 4 + 24 + 4 * 8 + 16 + 8 + 16 + 8 + (fmt ? 8 : 0));
   const int64_t per_spot = (int64_t)n_spots * (4 * 4 + 8 + 4) + (int64_t)2 * 152 * n_spots * 4;
