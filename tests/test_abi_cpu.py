@@ -68,6 +68,8 @@ def test_binding_error_constant_matches_header():
     text = open(os.path.join(ROOT, "include", "fredopt.h")).read()
     assert int(re.search(r"#define FREDOPT_ERR_TIMEOUT \((-?\d+)\)", text).group(1)) == fredopt.ERR_TIMEOUT
     assert 1 << int(re.search(r"#define FREDOPT_WAIT_POLLS \(1 << (\d+)\)", text).group(1)) == fredopt.WAIT_POLLS
+    assert int(re.search(r"#define FREDOPT_INDEX32 (0x[0-9a-fA-F]+)", text).group(1), 16) == fredopt.INDEX32
+    assert int(re.search(r"#define FREDOPT_ROWS_ROI (0x[0-9a-fA-F]+)", text).group(1), 16) == fredopt.ROWS["roi"]
 
 
 def test_kernels_compiled_for_sm_103a():
