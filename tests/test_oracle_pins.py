@@ -69,6 +69,74 @@ def test_worked_trial_loop():
             assert got[key] == pytest.approx(val, abs=1e-15), key
 
 
+@pytest.mark.parametrize("case", load_worked()["cases"], ids=lambda c: c["name"])
+def test_worked_violations(case):
+    """Row violations at the worked points, derived by hand: the amount an
+    upper bound is exceeded (a.x - b) or a lower bound missed (b - a.x), 0
+    when satisfied; LETd rows in Gy keV/um (R10)."""
+    P = small_problem(case["D"], case["L"], case["mask"], case["constraints"])
+    R = oracle.constraint_rows(P)
+    np.testing.assert_allclose(oracle.violations(R, case["x"]), case["expected_violations"], rtol=0, atol=1e-12)
+
+
+def test_worked_final_report():
+    """final_report on a hand-derived case: dose, Lw and LETd (Eq. 1, 0 where
+    the dose is 0), rows in constraint-table then voxel order with one row
+    per (structure, constraint) of an overlapping voxel (R11), unreachable
+    rows dropped (R10), the largest violation per constraint, the number of
+    violated rows and the Eq. 2 objective with its weight."""
+    t = load_worked()["report"]
+    P = small_problem(t["D"], t["L"], t["mask"], t["constraints"], t["objective"])
+    R = oracle.constraint_rows(P)
+    e = t["expected"]
+    np.testing.assert_array_equal(R.voxel, e["row_voxels"])
+    np.testing.assert_allclose(oracle.violations(R, t["w"]), e["row_violations"], rtol=0, atol=1e-12)
+    rep = oracle.final_report(P, t["w"], rows=R)
+    for k in ("dose", "lw", "letd"):
+        np.testing.assert_allclose(rep[k], e[k], rtol=0, atol=1e-12)
+    assert rep["max_violation"] == {int(k): pytest.approx(v, abs=1e-12) for k, v in e["max_violation"].items()}
+    assert rep["n_violated"] == e["n_violated"]
+    assert rep["unreachable"] == e["unreachable"]
+    assert rep["objective"] == pytest.approx(e["objective"], abs=1e-12)
+    # the same report without precomputed rows
+    rep2 = oracle.final_report(P, t["w"])
+    assert rep2["n_violated"] == e["n_violated"] and rep2["unreachable"] == e["unreachable"]
+
+
+def test_violations_sign_and_letd_units():
+    """Violations are nonnegative and zero exactly on the feasible side; in
+    physical units they are dose - bound (upper), bound - dose (lower),
+    bound - cDL (lower cDL) and, for a LETd row divided by the dose,
+    LETd - Lambda (R10, Eq. 1)."""
+    rng = np.random.default_rng(8)
+    D = rng.uniform(0.1, 1.0, (6, 4))
+    L = D * rng.uniform(1.0, 9.0, (6, 4))
+    cons = [dict(struct_bit=0, kind="DOSE_MAX", bound=2.0, priority=1.0),
+            dict(struct_bit=0, kind="DOSE_MIN", bound=1.0, priority=1.0),
+            dict(struct_bit=0, kind="LETD_MAX", bound=4.0, priority=1.0),
+            dict(struct_bit=0, kind="CDL_MIN", bound=0.1, priority=1.0)]
+    P = small_problem(D, L, np.ones(6, np.uint32), cons)
+    R = oracle.constraint_rows(P)
+    for _ in range(20):
+        x = rng.uniform(0.0, 2.0, 4)
+        v = oracle.violations(R, x)
+        ax = R.A @ x
+        assert np.all(v >= 0)
+        np.testing.assert_array_equal(v == 0, np.where(R.upper, ax <= R.b, ax >= R.b))
+        dose, lw = oracle.forward(P, x)
+        let = oracle.letd(dose, lw)
+        sel = R.cidx == 2
+        np.testing.assert_allclose(v[sel] / dose[R.voxel[sel]], np.maximum(let[R.voxel[sel]] - 4.0, 0.0),
+                                   rtol=1e-12, atol=1e-12)
+        sel = R.cidx == 0
+        np.testing.assert_allclose(v[sel], np.maximum(dose[R.voxel[sel]] - 2.0, 0.0), rtol=0, atol=1e-12)
+        sel = R.cidx == 1
+        np.testing.assert_allclose(v[sel], np.maximum(1.0 - dose[R.voxel[sel]], 0.0), rtol=0, atol=1e-12)
+        sel = R.cidx == 3
+        np.testing.assert_allclose(v[sel], np.maximum(0.1 - oracle.C_CDL * lw[R.voxel[sel]], 0.0), rtol=0,
+                                   atol=1e-12)
+
+
 # ------------------------------------------------------------ one half-space
 
 def _rand_row_problem(seed, kind, n=7):
