@@ -421,17 +421,19 @@ def robust_scenarios():
             for rs in (0.965, 1.0, 1.035)]
 
 
-def robust_plan(seed: int = 0, noise: float = 0.01, scenarios=None):
+def robust_plan(seed: int = 0, noise: float = 0.01, scenarios=None, shape=ROBUST_SHAPE, h=ROBUST_H,
+                spots: int = 16, layers: int = 16, pitch: float = 4.0):
     """Robust plan on the 120x120x100 phantom at 2.5 mm (two fields at 0 and
     90 degrees, 2 x 64 x 64 spots ... trimmed to 8192 spots: 16 x 16 lateral x
     16 layers per field): the rows of every scenario's influence matrices are
     stacked, so one spot-weight vector has to meet the constraints in all
     scenarios (structure masks follow the patient).  Returns (plan, nnz per
-    scenario)."""
+    scenario).  shape, h, spots, layers and pitch give smaller versions of the
+    same geometry (small_robust_plan)."""
     scen = robust_scenarios() if scenarios is None else scenarios
     parts, per = [], []
     for k, (shift, rs) in enumerate(scen):
-        pl = _sphere_plan("robust", ROBUST_SHAPE, ROBUST_H, 25.0, [0.0, 90.0], 16, 16, 4.0, seed, noise,
+        pl = _sphere_plan("robust", shape, h, 25.0, [0.0, 90.0], spots, layers, pitch, seed, noise,
                           shift_mm=shift, density_scale=rs)
         parts.append(pl)
         per.append(pl.nnz)
@@ -446,7 +448,15 @@ def robust_plan(seed: int = 0, noise: float = 0.01, scenarios=None):
     D = np.concatenate([pl.D for pl in parts])
     L = np.concatenate([pl.L for pl in parts])
     mask = np.tile(base.mask, len(parts))
-    plan = Plan(name="robust27", shape=(V * len(parts), 1, 1), h_mm=ROBUST_H, params=base.params, row_ptr=row_ptr,
+    plan = Plan(name=f"robust{len(parts)}", shape=(V * len(parts), 1, 1), h_mm=h, params=base.params, row_ptr=row_ptr,
                 col=col, D=D, L=L, mask=mask, structures=base.structures, constraints=base.constraints,
                 objective=base.objective, w0=base.w0.copy(), iters=100, alpha=0.99, relaxation=1.0)
     return plan, per
+
+
+def small_robust_plan(seed: int = 0, noise: float = 0.01, scenarios=None):
+    """The robust geometry at test size: the same 300 x 300 x 250 mm phantom
+    at 7.5 mm (40 x 40 x 34 voxels), two fields of 6 x 6 spots 8 mm apart x 6
+    layers (432 spots), all 27 scenarios stacked (about 2.9e6 nonzeros)."""
+    return robust_plan(seed=seed, noise=noise, scenarios=scenarios, shape=(40, 40, 34), h=7.5, spots=6,
+                       layers=6, pitch=8.0)
