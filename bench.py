@@ -238,8 +238,8 @@ def run_gpu_arm(args):
         return dict(ms=ms, kt=kt, launches=launches, clocks=clocks, rep=rep, sizes=sz, t_load=t_load,
                     fwd=fw, bwd=bw, w=w, dose=dose, letd=letd)
 
-    main = timed_run("all")
-    roi = timed_run("roi") if args.roi else None
+    main = timed_run("all", args.fmt)
+    roi = timed_run("roi", args.fmt) if args.roi else None
     prec = {}
     if args.precision:
         # FP64-class reference outputs: the double-float final pass of an FP32
@@ -327,7 +327,7 @@ def run_gpu_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "rows": "all voxel rows streamed every pass",
                        "n_vox": main["sizes"]["n_vox"], "n_spots": main["sizes"]["n_spots"],
-                       "nnz_per_matrix": main["sizes"]["nnz"], "storage": "fp32",
+                       "nnz_per_matrix": main["sizes"]["nnz"], "storage": args.fmt,
                        "l2": "inputs larger than L2 (each forward pass streams %.1f GB, each "
                              "transposed pass %.1f GB on average)" % (
                            main["fwd"]["bytes_per_launch"] / 1e9, main["bwd"]["bytes_per_launch"] / 1e9),
@@ -701,6 +701,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2.0, help="mean arrivals per second")
     ap.add_argument("--no-precision", dest="precision", action="store_false",
                     help="skip the BF16/FP16 storage runs")
+    ap.add_argument("--fmt", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="value storage of the main timed run (profiling of the 16-bit streams)")
     ap.add_argument("--small", action="store_true",
                     help="half-resolution phantom (100x100x75 at 4 mm) for profiler captures")
     ap.add_argument("--batching", action="store_true",
