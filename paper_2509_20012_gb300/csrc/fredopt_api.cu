@@ -1082,8 +1082,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     if (!(format & FREDOPT_INDEX32)) {
       const int64_t n_cblk = nh_alloc / 128;
       CK(h->crow16.alloc(nh_alloc));
-      CK(h->chdr.alloc(n_cblk + kHdrPad));
-      CK(cudaMemsetAsync(h->chdr.p + n_cblk, 0, kHdrPad * sizeof(int32_t), s));
+      CK(h->chdr.alloc(n_cblk));
       CK(h->cnw.ensure(2));
       CK(cudaMemsetAsync(h->cnw.p, 0, 2 * sizeof(unsigned int), s));
       launch_narrow_rows(h->crow.p, n_cblk, h->crow16.p, h->chdr.p, h->cnw.p, s);

@@ -27,9 +27,6 @@ constexpr int kMaxCon = 32;
 // elements of zero padding after the last nonzero of every index/value array
 // (covers the block alignment and the prefetched unit of the streaming loop)
 constexpr int64_t kPadElems = 1024;
-// extra zero headers after the block-header table of based 16-bit row
-// indices (staged copies of a stage's headers start at a 16-byte boundary)
-constexpr int64_t kHdrPad = 16;
 constexpr int kMaxObj = 32;
 
 // constraint kinds (same numbering as the public header)

@@ -64,34 +64,6 @@ constexpr int kBwdUnroll = FO_BWD_UNROLL;
 #ifndef FO_BWD_PP
 #define FO_BWD_PP 0
 #endif
-// Shared-memory staging of the transposed product's streams: each warp keeps
-// a ring of stages, each one unit (U blocks of 128 elements) of the index
-// and value streams (and the unit's block headers), filled by bulk (TMA)
-// copies issued stages ahead, so a warp's loop waits only on its coefficient
-// gathers.  FO_BWD_STAGE_BYTES is the ring size per warp (the stage count is
-// that over the stage size, clamped to [2, 4]); 0 keeps register loads.
-#ifndef FO_BWD_STAGE_BYTES
-#define FO_BWD_STAGE_BYTES 0
-#endif
-// how a stage is filled: 0 bulk (TMA) copies completing on an mbarrier per
-// stage; 1 16-byte cp.async copies of all lanes, one commit group per stage
-#ifndef FO_BWD_STAGE_KIND
-#define FO_BWD_STAGE_KIND 1
-#endif
-// how a warp waits for a bulk-copied stage: 0 mbarrier.try_wait (may suspend
-// the warp), 1 mbarrier.test_wait polled without suspending
-#ifndef FO_BWD_WAIT_KIND
-#define FO_BWD_WAIT_KIND 0
-#endif
-// 1: the stage also carries the block headers of based row offsets; 0: the
-// headers are read with plain loads
-#ifndef FO_BWD_HDR_STAGE
-#define FO_BWD_HDR_STAGE 1
-#endif
-// register units (U blocks each) per stage: the size of one bulk copy
-#ifndef FO_BWD_STAGE_UNITS
-#define FO_BWD_STAGE_UNITS 2
-#endif
 constexpr int kFwdUnroll16 = FO_UNROLL16;
 constexpr int kBwdUnroll16 = FO_BWD_UNROLL16;
 constexpr bool kBwdPingPong = FO_BWD_PP != 0;
@@ -100,9 +72,6 @@ constexpr int kBwdThreads = 256;
 constexpr int kRowThreads = 256;
 constexpr int kColThreads = 256;
 constexpr int kMbarSpins = FREDOPT_WAIT_POLLS;
-// polls of a staged stream's wait without suspending (a test_wait takes tens
-// of ns: about 0.1-0.3 s in all)
-constexpr int kStagePolls = 1 << 22;
 // Lane mapping of a block's 128 elements (element of value q of lane l):
 //   0 contiguous  4l + q            (16-byte index / FP32 loads per lane)
 //   1 strided     32q + l           (one gather instruction reads the
@@ -287,58 +256,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// the same with an L2 evict-first hint (streamed data read once per pass)
-__device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                                uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
-      "%4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-      : "memory");
-}
 // bulk prefetch of [src, src + bytes) into L2 (TMA engine; no registers or
 // shared memory; bytes a multiple of 16, src 16-byte aligned)
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-// 16-byte asynchronous copy global -> shared through L2 only (cp.async.cg)
-// with an L2 evict-first hint; completes in the thread's current commit group
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint64_t pol) {
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-               "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most n of the thread's commit groups are pending (n < 8)
-__device__ __forceinline__ void cp_async_wait(int n) {
-  switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
-    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
-    case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
-  }
-}
-// bounded poll of phase `parity` without suspending the thread; true when
-// the phase completed
-__device__ __forceinline__ bool mbar_poll(uint64_t* bar, uint32_t parity, int max_polls) {
-  const uint32_t a = smem_u32(bar);
-  for (int i = 0; i < max_polls; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
 }
 // bounded wait on phase `parity`; true when the phase completed
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_spins) {
@@ -390,51 +311,6 @@ struct SegCheck {
   int64_t n_elems;
   int* err;
 };
-
-// Per-warp ring of shared-memory stages of the staged stream (stream_segments
-// with NS > 0).  A stage holds SU units (SU * U blocks of 128 elements) of
-// the index stream, the A and B value streams and the stage's block headers
-// (StageLayout), filled by bulk copies that complete on the stage's
-// mbarrier.  n_issued / n_used count the stages the warp has issued /
-// consumed over all of its tiles: stage n lives in slot n % NS and completes
-// phase (n / NS) & 1 of its barrier.
-struct StageRing {
-  unsigned char* buf;
-  uint64_t* bar;
-  uint32_t n_issued, n_used;
-  bool failed;  // a bounded wait gave up
-};
-template <typename VT, typename IT, bool USE_A, bool BASED, int U, int SU>
-struct StageLayout {
-  static constexpr int UB = U * 128;        // elements of a register unit
-  static constexpr int SB = SU * UB;        // elements of a stage
-  static constexpr int kIdx = 0;
-  static constexpr int kA = SB * (int)sizeof(IT);
-  static constexpr int kB = kA + (USE_A ? SB * (int)sizeof(VT) : 0);
-  static constexpr int kH = kB + SB * (int)sizeof(VT);
-  // headers of the stage's SU * U blocks, copied from the 16-byte boundary
-  // at or below the first one (up to 3 more in front)
-  static constexpr int kHdrBytes = ((SU * U + 3 + 3) / 4) * 16;
-  static constexpr int kBytes = kH + (BASED && FO_BWD_HDR_STAGE ? kHdrBytes : 0);
-  static_assert(kA % 16 == 0 && kB % 16 == 0 && kH % 16 == 0, "bulk copies need 16-byte offsets");
-};
-// Stage count of a per-warp ring of `budget` bytes (0: no staging).
-constexpr int stage_count(int stage_bytes, int budget) {
-  return budget <= 0 ? 0 : (budget / stage_bytes < 2 ? 2 : (budget / stage_bytes > 4 ? 4 : budget / stage_bytes));
-}
-// A pair block (elements p, p + 1, p + 64, p + 65 with p = 2 lane) read from
-// a staged block in shared memory.
-template <typename T>
-__device__ __forceinline__ uint4 lds_pairs(const unsigned char* blk, int lane) {
-  if constexpr (sizeof(T) == 4) {
-    const uint2* q = reinterpret_cast<const uint2*>(blk);
-    const uint2 a = q[lane], b = q[32 + lane];
-    return make_uint4(a.x, a.y, b.x, b.y);
-  } else {
-    const unsigned* q = reinterpret_cast<const unsigned*>(blk);
-    return make_uint4(q[lane], q[32 + lane], 0u, 0u);
-  }
-}
 
 template <bool S>
 __device__ __forceinline__ int4 ld_idx(const int32_t* p) {
@@ -538,15 +414,13 @@ __device__ __forceinline__ void load_blk_pairs(Blk<VT>& k, const IT* idx, const 
 // round_up(ptr[r1], 32*V) + U*32*V elements (a prefetch starts below ptr[r1]
 // and covers U*32*V elements, within the same bound).
 template <typename VT, typename Acc, bool S, bool USE_A, int U, bool BASED = false, int LM = 0,
-          typename IT, class Gather, class Flush, int PF = kPrefetchUnits, bool PP = false, int NS = 0,
-          int SU = 1>
+          typename IT, class Gather, class Flush, int PF = kPrefetchUnits, bool PP = false>
 __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
                                                 const VT* __restrict__ Av, const VT* __restrict__ Bv,
                                                 const int64_t* __restrict__ ptr, int64_t r0, int64_t r1,
                                                 int lane, Gather gather, Flush flush,
                                                 BlockBase bbase = BlockBase{nullptr, nullptr, 0},
-                                                SegCheck chk = SegCheck{0, nullptr},
-                                                StageRing* ring = nullptr) {
+                                                SegCheck chk = SegCheck{0, nullptr}) {
   constexpr int V = VecOf<VT>::V;
   constexpr int BLK = 32 * V;
   constexpr int UB = U * BLK;
@@ -667,109 +541,6 @@ __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
   };
 
   int b = 0;
-  if constexpr (NS > 0) {
-    // Staged: stages [sb, sb + SB) for sb <= pe are copied into the warp's
-    // ring NS stages ahead of their use (the unit at b = pe can hold trailing
-    // empty segments; stages not consumed are drained at the end, so no copy
-    // is in flight when the warp moves on).  A slot is refilled only after
-    // the values read from it were consumed, behind a proxy fence.  Every
-    // wait is bounded: if one gives up, ring->failed is set and the warp
-    // stops after draining.
-    using SL = StageLayout<VT, IT, USE_A, BASED, U, SU>;
-    constexpr int SB = SL::SB;
-    static_assert(LM == 2 && BLK == 128 && SL::UB == UB, "staged stream: pair mapping, 128-element blocks");
-    // a stage at sb <= pe reads at most SB elements past the last nonzero and
-    // SL::kHdrBytes / 4 headers from the 4-aligned block at or below it: the
-    // zero padding of the streams and of the header table covers both
-    static_assert(SB <= kPadElems && SL::kHdrBytes / 4 <= kPadElems / 128 + kHdrPad, "stage past the padding");
-    const int64_t blk0 = start / BLK;
-    const int32_t* __restrict__ hdr_g = BASED ? bbase.hdr : nullptr;
-    const uint64_t pol = l2_evict_first_policy();
-    auto issue = [&](int q) {
-      if (FO_BWD_STAGE_KIND == 1) {
-        // every lane copies 16-byte chunks lane, lane + 32, ... of each stream
-        unsigned char* st = ring->buf + (size_t)(ring->n_issued % NS) * SL::kBytes;
-        auto copy = [&](int off, const void* src, int bytes) {
-          const unsigned char* g = reinterpret_cast<const unsigned char*>(src);
-#pragma unroll
-          for (int c = lane * 16; c < bytes; c += 32 * 16) cp_async16(st + off + c, g + c, pol);
-        };
-        copy(SL::kIdx, idx + q, SB * (int)sizeof(IT));
-        if (USE_A) copy(SL::kA, Av + q, SB * (int)sizeof(VT));
-        copy(SL::kB, Bv + q, SB * (int)sizeof(VT));
-        if (BASED && FO_BWD_HDR_STAGE && lane * 16 < SL::kHdrBytes)
-          cp_async16(st + SL::kH + lane * 16, hdr_g + ((blk0 + q / BLK) & ~(int64_t)3) + lane * 4);
-        cp_async_commit();
-        ++ring->n_issued;
-        return;
-      }
-      if (lane == 0) {
-        const uint32_t slot = ring->n_issued % NS;
-        unsigned char* st = ring->buf + (size_t)slot * SL::kBytes;
-        uint64_t* bar = ring->bar + slot;
-        // the slot's previous values were read through the generic proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, (uint32_t)SL::kBytes);
-        bulk_g2s_stream(st + SL::kIdx, idx + q, (uint32_t)(SB * sizeof(IT)), bar, pol);
-        if (USE_A) bulk_g2s_stream(st + SL::kA, Av + q, (uint32_t)(SB * sizeof(VT)), bar, pol);
-        bulk_g2s_stream(st + SL::kB, Bv + q, (uint32_t)(SB * sizeof(VT)), bar, pol);
-        if (BASED && FO_BWD_HDR_STAGE)
-          bulk_g2s(st + SL::kH, hdr_g + ((blk0 + q / BLK) & ~(int64_t)3), (uint32_t)SL::kHdrBytes, bar);
-      }
-      ++ring->n_issued;
-    };
-    auto wait_next = [&]() -> const unsigned char* {
-      const uint32_t slot = ring->n_used % NS;
-      if (FO_BWD_STAGE_KIND == 1) {
-        // the oldest pending group of every lane, then all lanes' copies
-        cp_async_wait((int)(ring->n_issued - ring->n_used - 1));
-        __syncwarp();
-        ++ring->n_used;
-        return ring->buf + (size_t)slot * SL::kBytes;
-      }
-      const bool ok = FO_BWD_WAIT_KIND == 1 ? mbar_poll(ring->bar + slot, (ring->n_used / NS) & 1u, kStagePolls)
-                                             : mbar_wait(ring->bar + slot, (ring->n_used / NS) & 1u, kMbarSpins);
-      ++ring->n_used;
-      if (!ok) ring->failed = true;
-      return ok ? ring->buf + (size_t)slot * SL::kBytes : nullptr;
-    };
-    for (int k = 0; k < NS && k * SB <= pe; ++k) issue(k * SB);
-    Blk<VT> ua[U];
-    int sb = 0;
-    while (!done) {
-      const unsigned char* st = wait_next();
-      if (st == nullptr) break;
-      const int hsh = (int)((blk0 + sb / BLK) & 3);
-#pragma unroll 1
-      for (int su = 0; su < SU && !done; ++su) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int j = su * U + u;  // block of the stage
-          const uint4 c = lds_pairs<IT>(st + SL::kIdx + j * BLK * (int)sizeof(IT), lane);
-          ua[u].c0 = make_int4((int)c.x, (int)c.y, (int)c.z, (int)c.w);
-          if (USE_A) ua[u].a = lds_pairs<VT>(st + SL::kA + j * BLK * (int)sizeof(VT), lane);
-          ua[u].b = lds_pairs<VT>(st + SL::kB + j * BLK * (int)sizeof(VT), lane);
-          if (BASED) {
-            if (FO_BWD_HDR_STAGE) ua[u].hb = reinterpret_cast<const int32_t*>(st + SL::kH)[hsh + j];
-            else ua[u].hb = __ldg(hdr_g + blk0 + sb / BLK + j);
-          }
-        }
-        consume(ua, b);
-        b += UB;
-      }
-      if (done) break;
-      __syncwarp();
-      if (sb + NS * SB <= pe) issue(sb + NS * SB);
-      if (PF > 0 && lane == 0 && sb + (NS + PF) * SB < pe) {
-        const int q = sb + (NS + PF) * SB;
-        bulk_prefetch_l2(idx + q, (uint32_t)(SB * sizeof(IT)));
-        if (USE_A) bulk_prefetch_l2(Av + q, (uint32_t)(SB * sizeof(VT)));
-        bulk_prefetch_l2(Bv + q, (uint32_t)(SB * sizeof(VT)));
-      }
-      sb += SB;
-    }
-    while (ring->n_used != ring->n_issued) wait_next();
-  } else {
 #pragma unroll
   for (int k = 1; k < PF; ++k) prefetch_unit(b + k * UB);
   if (PP) {
@@ -796,7 +567,6 @@ __device__ __forceinline__ void stream_segments(const IT* __restrict__ idx,
       consume(ua, b);
       b += UB;
     }
-  }
   }
 }
 
@@ -947,35 +717,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1024 / kFwdThreads) k_forward(Fwd
 // Chunk sums of the transposed product: chunk c = nonzeros [chunk_ptr[c],
 // chunk_ptr[c+1]) of one column; sum_i D_ij coef_i.x + L_ij coef_i.y.
 // NB: row indices as based 16-bit offsets (BwdArgs.row16/hdr/ovf).
-template <typename VT, bool UD, bool NB>
-struct BwdStage {
-  using IT = typename std::conditional<NB, uint16_t, int32_t>::type;
-  static constexpr int U = sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16;
-  static constexpr int SU = FO_BWD_STAGE_UNITS;
-  using SL = StageLayout<VT, IT, UD, NB, U, SU>;
-  static constexpr int NS = stage_count(SL::kBytes, FO_BWD_STAGE_BYTES);
-  // dynamic shared memory of one CTA: each warp's NS stages, then its NS barriers
-  static constexpr int kSmem = NS > 0 ? (kBwdThreads / 32) * NS * (SL::kBytes + 8) : 0;
-};
-
 template <typename VT, bool S, bool UD, bool NB>
 __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(BwdArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  using BS = BwdStage<VT, UD, NB>;
-  constexpr int NS = BS::NS;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  StageRing ring{nullptr, nullptr, 0u, 0u, false};
-  if constexpr (NS > 0) {
-    const int wib = threadIdx.x >> 5;
-    ring.buf = smem + (size_t)wib * NS * BS::SL::kBytes;
-    ring.bar = reinterpret_cast<uint64_t*>(smem + (size_t)(kBwdThreads / 32) * NS * BS::SL::kBytes) + wib * NS;
-    if (lane == 0) {
-      for (int i = 0; i < NS; ++i) mbar_init(ring.bar + i, 1);
-      fence_mbar_init();
-    }
-    __syncwarp();
-  }
   const VT* __restrict__ Dv = reinterpret_cast<const VT*>(a.Dv);
   const VT* __restrict__ Lv = reinterpret_cast<const VT*>(a.Lv);
   const float2* __restrict__ cf = a.coef;
@@ -1002,21 +747,15 @@ __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(Bwd
   int job = a.sched ? claim() : warp;
   while (job < a.n_warps) {
     if (NB)
-      stream_segments<VT, float, S, UD, BS::U, true, kBwdLaneMap<VT>, uint16_t, decltype(gather),
-                      decltype(flush), kPrefetchUnits, kBwdPingPong, NS, BS::SU>(
+      stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16), true, kBwdLaneMap<VT>,
+                      uint16_t, decltype(gather), decltype(flush), kPrefetchUnits, kBwdPingPong>(
           a.row16, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush,
-          BlockBase{a.hdr, a.ovf, a.n_ovf}, SegCheck{a.n_elems, FO_CHECKED ? &a.st->err : nullptr}, &ring);
+          BlockBase{a.hdr, a.ovf, a.n_ovf}, SegCheck{a.n_elems, FO_CHECKED ? &a.st->err : nullptr});
     else
-      stream_segments<VT, float, S, UD, BS::U, false, kBwdLaneMap<VT>, int32_t, decltype(gather),
-                      decltype(flush), kPrefetchUnits, kBwdPingPong, NS, BS::SU>(
+      stream_segments<VT, float, S, UD, (sizeof(VT) == 4 ? kBwdUnroll : kBwdUnroll16), false, kBwdLaneMap<VT>,
+                      int32_t, decltype(gather), decltype(flush), kPrefetchUnits, kBwdPingPong>(
           a.row, Dv, Lv, a.chunk_ptr, a.warp_chunk[job], a.warp_chunk[job + 1], lane, gather, flush,
-          BlockBase{nullptr, nullptr, 0}, SegCheck{a.n_elems, FO_CHECKED ? &a.st->err : nullptr}, &ring);
-    if (NS > 0 && ring.failed) {
-      // a bounded wait gave up: report it and stop (the host clears the
-      // error word and the tile counters)
-      if (lane == 0) atomicOr(&a.st->err, 1);
-      return;
-    }
+          BlockBase{nullptr, nullptr, 0}, SegCheck{a.n_elems, FO_CHECKED ? &a.st->err : nullptr});
     if (!a.sched) break;
     job = claim();
   }
@@ -1785,13 +1524,12 @@ void launch_forward(const Geometry& g, int fmt, int epi, bool stream_hint, const
 
 template <typename VT, bool NB>
 static void bwd_dispatch_nb(const Geometry& g, bool st, bool ud, const BwdArgs& a, cudaStream_t s) {
-  constexpr int smU = BwdStage<VT, true, NB>::kSmem, smG = BwdStage<VT, false, NB>::kSmem;
   if (st) {
-    if (ud) k_backward<VT, true, true, NB><<<g.bwd_blocks, g.bwd_threads, smU, s>>>(a);
-    else k_backward<VT, true, false, NB><<<g.bwd_blocks, g.bwd_threads, smG, s>>>(a);
+    if (ud) k_backward<VT, true, true, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+    else k_backward<VT, true, false, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
   } else {
-    if (ud) k_backward<VT, false, true, NB><<<g.bwd_blocks, g.bwd_threads, smU, s>>>(a);
-    else k_backward<VT, false, false, NB><<<g.bwd_blocks, g.bwd_threads, smG, s>>>(a);
+    if (ud) k_backward<VT, false, true, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
+    else k_backward<VT, false, false, NB><<<g.bwd_blocks, g.bwd_threads, 0, s>>>(a);
   }
 }
 template <typename VT>
@@ -2016,32 +1754,6 @@ static cudaError_t set_smem_all(int bytes) {
   return set_smem_attr<VT, EPI_FINAL>(bytes);
 }
 
-// Dynamic shared memory of the staged transposed product: allow it for every
-// instantiation and return the largest (0 without staging).
-template <typename VT, bool S, bool UD, bool NB>
-static cudaError_t bwd_smem_attr(int* mx) {
-  constexpr int b = BwdStage<VT, UD, NB>::kSmem;
-  if (b > *mx) *mx = b;
-  if (b == 0) return cudaSuccess;
-  // as much shared memory as the SM has, so every CTA of the grid is resident
-  cudaError_t e = cudaFuncSetAttribute(k_backward<VT, S, UD, NB>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess || b <= 48 * 1024) return e;
-  return cudaFuncSetAttribute(k_backward<VT, S, UD, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-}
-template <typename VT>
-static cudaError_t bwd_smem_all(int* mx) {
-  cudaError_t e;
-  if ((e = bwd_smem_attr<VT, true, true, true>(mx)) != cudaSuccess) return e;
-  if ((e = bwd_smem_attr<VT, true, false, true>(mx)) != cudaSuccess) return e;
-  if ((e = bwd_smem_attr<VT, false, true, true>(mx)) != cudaSuccess) return e;
-  if ((e = bwd_smem_attr<VT, false, false, true>(mx)) != cudaSuccess) return e;
-  if ((e = bwd_smem_attr<VT, true, true, false>(mx)) != cudaSuccess) return e;
-  if ((e = bwd_smem_attr<VT, true, false, false>(mx)) != cudaSuccess) return e;
-  if ((e = bwd_smem_attr<VT, false, true, false>(mx)) != cudaSuccess) return e;
-  return bwd_smem_attr<VT, false, false, false>(mx);
-}
-
 int init_kernels(Geometry* g, int device) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return -1;
@@ -2052,16 +1764,8 @@ int init_kernels(Geometry* g, int device) {
   // for 30000 spots); smaller CTAs only when it is read through L1 instead
   g->fwd_blocks = g->n_sms * (FO_FWD_XS ? 1 : 1024 / kFwdThreads);
   g->fwd_warps = g->fwd_blocks * (kFwdThreads / 32);
-  // one grid for every instantiation of the transposed product (static
-  // tiles need a warp per tile): the occupancy of the one with the most
-  // shared memory
-  int bwd_smem = 0;
-  if (bwd_smem_all<float>(&bwd_smem) != cudaSuccess) return -2;
-  if (bwd_smem_all<__nv_bfloat16>(&bwd_smem) != cudaSuccess) return -2;
-  if (bwd_smem_all<__half>(&bwd_smem) != cudaSuccess) return -2;
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<float, true, true, false>, kBwdThreads,
-                                                (size_t)bwd_smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<float, true, true, false>, kBwdThreads, 0);
   if (occ < 1) occ = 1;
   g->bwd_threads = kBwdThreads;
   g->bwd_blocks = g->n_sms * occ;
