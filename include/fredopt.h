@@ -357,6 +357,15 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);
  * -1 for a null handle. */
 int64_t fredopt_launch_count(fredopt_t h);
 
+/* Architecture of the library's code for `device`, as the CUDA runtime
+ * reports it for the kernels it would launch there (cudaFuncGetAttributes):
+ * the binary (SASS) version of the forward product and of the transposed
+ * product, and the PTX version, each major * 10 + minor (103 for sm_103a).
+ * Any pointer may be NULL.  Returns FREDOPT_OK, or FREDOPT_ERR_CUDA when no
+ * usable device or code object is found.  The current device is left
+ * unchanged. */
+int fredopt_kernel_arch(int device, int* fwd_binary, int* bwd_binary, int* ptx_version);
+
 /* Polls of one device-side wait before it gives up: about 1 s on GB300
  * (a failed poll suspends about 4 us); a bulk copy completes in microseconds. */
 #define FREDOPT_WAIT_POLLS (1 << 18)
@@ -513,9 +522,14 @@ int fredopt_server_destroy(fredopt_server_t s);
  * FREDOPT_ERR_SHAPE.  Row indices outside [0, n_rows) are skipped and
  * column pointers are clamped to [0, nnz], so malformed input cannot read
  * outside the arrays.  The first call on a device looks up the scratch
- * address for that device.  All calls share the one scratch array: calls
- * that overlap on the GPU (other streams, other host threads) race and must
- * be serialised by the caller.  The result is deterministic. */
+ * address for that device (set-up once per device, with that device
+ * current); make that first call before any stream capture.  The address is
+ * kept until the process exits: after a cudaDeviceReset this entry point
+ * must not be called again in the process.  All calls share the one scratch
+ * array, which keeps the last call's contents (each call rewrites what it
+ * reads): calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  The result is deterministic:
+ * the same inputs give the same bits. */
 int fredopt_backward_noalloc(int64_t n_rows, int32_t n_cols, int64_t nnz, const int64_t* col_ptr,
                              const int32_t* row, const float* D_val, const float* L_val,
                              const float* a_D, const float* a_L, float* u_out, void* cuda_stream);

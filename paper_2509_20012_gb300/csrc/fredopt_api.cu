@@ -1927,6 +1927,21 @@ int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches) {
 
 int64_t fredopt_launch_count(fredopt_t h) { return h ? h->launches : -1; }
 
+int fredopt_kernel_arch(int device, int* fwd_binary, int* bwd_binary, int* ptx_version) {
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return FREDOPT_ERR_CUDA;
+  }
+  const cudaError_t e = kernel_arch(fwd_binary, bwd_binary, ptx_version);
+  cudaSetDevice(cur);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FREDOPT_ERR_CUDA;
+  }
+  return FREDOPT_OK;
+}
+
 int fredopt_check_wait(fredopt_t h, int arrive, int spins, float* elapsed_ms) {
   if (!h) return FREDOPT_ERR_INVALID_ARG;
   if (spins < 0) return fail(h, FREDOPT_ERR_INVALID_ARG, "spins must be >= 0");

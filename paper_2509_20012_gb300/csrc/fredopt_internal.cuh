@@ -185,6 +185,9 @@ struct Geometry {
 };
 
 int init_kernels(Geometry* g, int device);  // sets function attributes once per device
+// binary and PTX architecture versions (major * 10 + minor) of the loaded
+// forward and transposed-product kernels on the current device
+cudaError_t kernel_arch(int* fwd_binary, int* bwd_binary, int* ptx_version);
 
 bool forward_uses_smem(const Geometry& g, int n_x_pad);
 void launch_forward(const Geometry& g, int fmt, int epi, bool stream_hint, const FwdArgs& a,

@@ -1775,6 +1775,18 @@ static cudaError_t set_smem_all(int bytes) {
   return set_smem_attr<VT, EPI_FINAL>(bytes);
 }
 
+cudaError_t kernel_arch(int* fwd_binary, int* bwd_binary, int* ptx_version) {
+  cudaFuncAttributes fa, ba;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_forward<float, EPI_OBJ, true, true, uint16_t>);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncGetAttributes(&ba, k_backward<float, true, true, true>);
+  if (e != cudaSuccess) return e;
+  if (fwd_binary) *fwd_binary = fa.binaryVersion;
+  if (bwd_binary) *bwd_binary = ba.binaryVersion;
+  if (ptx_version) *ptx_version = fa.ptxVersion;
+  return cudaSuccess;
+}
+
 int init_kernels(Geometry* g, int device) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return -1;

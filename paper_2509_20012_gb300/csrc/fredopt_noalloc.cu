@@ -39,7 +39,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
 void* g_na_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch on the current device (set-up once per device).
+// Device address of the scratch on the current device, looked up once per
+// device (cudaGetSymbolAddress with that device current) and kept for the
+// life of the process.  A cudaDeviceReset reloads the module, so the kept
+// address is no longer valid after one.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -150,9 +153,13 @@ extern "C" int fredopt_backward_noalloc(int64_t n_rows, int32_t n_cols, int64_t 
   int32_t* off = reinterpret_cast<int32_t*>(base);
   float* part = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(base) + kNaOffBytes);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // grid of the chunk kernel: 8 CTAs per SM (152 SMs on GB300 if the query fails)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 152;
+  }
   k_na_offsets<<<1, 1024, 0, s>>>(col_ptr, n_cols, nnz, off);
   k_na_chunks<<<sms * 8, 256, 0, s>>>(col_ptr, row, D_val, L_val, a_D, a_L, n_rows, n_cols, nnz, off, part);
   k_na_columns<<<(n_cols + 255) / 256, 256, 0, s>>>(off, part, n_cols, u_out);

@@ -156,6 +156,7 @@ _SIGS = {
     "fredopt_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fredopt_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fredopt_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "fredopt_kernel_arch": (ctypes.c_int, [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3),
     "fredopt_get_storage": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3),
     "fredopt_check_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "fredopt_footprint_bytes": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int]),
@@ -546,6 +547,17 @@ class Handle:
         r, c = ctypes.c_int64(), ctypes.c_int64()
         self._check(self.lib.fredopt_get_tuning(self.h, ctypes.byref(r), ctypes.byref(c)))
         return r.value, c.value
+
+
+def kernel_arch(device: int = 0):
+    """(forward binary, transposed-product binary, PTX) architecture versions
+    of the library's kernels on `device` (fredopt_kernel_arch; 103 = sm_103)."""
+    lib = load_library()
+    v = [ctypes.c_int() for _ in range(3)]
+    rc = lib.fredopt_kernel_arch(int(device), *[ctypes.byref(x) for x in v])
+    if rc != OK:
+        raise FredoptError(rc, lib.fredopt_strerror(rc).decode())
+    return tuple(x.value for x in v)
 
 
 def footprint_bytes(n_vox, n_spots, nnz, fmt="fp32") -> int:

@@ -596,3 +596,11 @@ def test_final_pass_is_fp64_product_of_fp32_inputs(lib, tiny):
     sel = d_ref > 0
     np.testing.assert_allclose(letd[sel], lt_ref[sel].astype(np.float32), rtol=2 ** -22, atol=0)
     assert np.all(letd[~sel] == 0)
+
+
+def test_loaded_code_is_sm_103a(lib):
+    """The code object the CUDA runtime loads for the hot kernels is sm_103a
+    SASS (cudaFuncGetAttributes binaryVersion 103), not a JIT of PTX for
+    another architecture."""
+    fwd, bwd, ptx = lib.kernel_arch(0)
+    assert fwd == 103 and bwd == 103, (fwd, bwd, ptx)
