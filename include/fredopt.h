@@ -482,7 +482,14 @@ typedef struct fredopt_ticket_info {
 
 typedef struct fredopt_server* fredopt_server_t;
 
-/* Upper estimate of the device memory one plan needs while it loads and runs. */
+/* Estimate of the device memory one plan needs while it loads and runs: the
+ * peak of the load and the resident CSR, CSC, based row offsets with their
+ * block headers, vectors and tables.  The overflow table of wide 128-element
+ * blocks (rows spanning 65536 or more) is counted for one such block per
+ * column boundary plus one in 16 blocks; for plans with sparser rows the
+ * estimate can be low, and a load that then does not fit fails with
+ * FREDOPT_ERR_OOM without disturbing the plans in flight.  The server admits
+ * requests while the sum of these estimates stays under its cap. */
 int64_t fredopt_footprint_bytes(int64_t n_vox, int32_t n_spots, int64_t nnz, int format);
 
 int fredopt_server_create(fredopt_server_t* out, int device, int64_t mem_cap_bytes, int max_active,

@@ -245,7 +245,15 @@ int64_t fredopt_footprint_bytes(int64_t n_vox, int32_t n_spots, int64_t nnz, int
   // peaks of the load: FP32 upload + gathered copy; then, while the 16-bit
   // index copies are made, CSR + CSC (int32 indices) + both 16-bit copies
   const int64_t load_peak = std::max(2 * na * 12, na * (2 * (4 + 2 * vb) + 4));
-  const int64_t resident = na * (4 + 2 * vb) * 2 + (fmt ? na * 8 : 0);
+  // resident: CSR with 16-bit columns and CSC with int32 and based 16-bit
+  // rows (as much as two int32 copies), the 16-bit copies' FP32 staging, the
+  // block headers of the based rows, and their overflow table for wide blocks
+  // (one per column boundary plus one in 16 blocks; a plan whose rows are
+  // sparser than that can exceed the estimate, and its load then fails with
+  // FREDOPT_ERR_OOM without disturbing the plans in flight)
+  const int64_t headers = na / 128 * 4;
+  const int64_t overflow = ((int64_t)n_spots + na / 128 / 16) * 128 * 4;
+  const int64_t resident = na * (4 + 2 * vb) * 2 + (fmt ? na * 8 : 0) + headers + overflow;
   const int64_t per_row = n_vox * (8 + 8 + 4 + 24 + 4 * 8 + 16 + 8 + 16 + 8 + (fmt ? 8 : 0));
   const int64_t per_spot = (int64_t)n_spots * (4 * 4 + 8 + 4) + (int64_t)2 * 152 * n_spots * 4;
   const int64_t tables = na / 256 * 16 + ((int64_t)16 << 20);
