@@ -411,6 +411,16 @@ int fredopt_get_tuning(fredopt_t h, int64_t* row_cost, int64_t* chunk_cost);
  * returns the device time of the iterate calls), fredopt_end per handle. */
 typedef struct fredopt_batch* fredopt_batch_t;
 int fredopt_batch_create(fredopt_batch_t* out, const fredopt_t* handles, int n);
+/* The same with a second graph of `depth` iterations of every plan (1 <=
+ * depth <= FREDOPT_BATCH_MAX_DEPTH): fredopt_batch_iterate replays it
+ * iters / depth times and the one-iteration graph for the rest, so a batch of
+ * small, launch-bound plans pays one graph launch per `depth` iterations.
+ * Each plan's kernels run in the same order as alone: results are
+ * bit-identical for every depth.  fredopt_superiorize_batch uses depth
+ * min(iters, FREDOPT_BATCH_DEPTH). */
+#define FREDOPT_BATCH_MAX_DEPTH 64
+#define FREDOPT_BATCH_DEPTH 10
+int fredopt_batch_create_depth(fredopt_batch_t* out, const fredopt_t* handles, int n, int depth);
 int fredopt_batch_iterate(fredopt_batch_t b, int iters);
 int fredopt_batch_sync(fredopt_batch_t b, double* device_ms);
 int fredopt_batch_destroy(fredopt_batch_t b);

@@ -2045,8 +2045,11 @@ struct fredopt_batch {
   cudaStream_t root = nullptr;
   std::vector<fredopt_t> hs;
   std::vector<int> nodes;
-  cudaGraph_t graph = nullptr;
+  cudaGraph_t graph = nullptr;      // one iteration of every plan
   cudaGraphExec_t exec = nullptr;
+  int depth = 1;                    // iterations of every plan in graph_k
+  cudaGraph_t graph_k = nullptr;
+  cudaGraphExec_t exec_k = nullptr;
   cudaEvent_t fork = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
   std::vector<cudaEvent_t> joins;
   double ms = 0.0;
@@ -2058,6 +2061,8 @@ void batch_free(fredopt_batch* b) {
   if (b->root) cudaStreamSynchronize(b->root);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->exec_k) cudaGraphExecDestroy(b->exec_k);
+  if (b->graph_k) cudaGraphDestroy(b->graph_k);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   for (cudaEvent_t e : {b->fork, b->done, b->t0, b->t1})
     if (e) cudaEventDestroy(e);
@@ -2069,7 +2074,11 @@ void batch_free(fredopt_batch* b) {
 extern "C" {
 
 int fredopt_batch_create(fredopt_batch_t* out, const fredopt_t* handles, int n) {
-  if (!out || !handles || n < 1) return FREDOPT_ERR_INVALID_ARG;
+  return fredopt_batch_create_depth(out, handles, n, 1);
+}
+
+int fredopt_batch_create_depth(fredopt_batch_t* out, const fredopt_t* handles, int n, int depth) {
+  if (!out || !handles || n < 1 || depth < 1 || depth > FREDOPT_BATCH_MAX_DEPTH) return FREDOPT_ERR_INVALID_ARG;
   *out = nullptr;
   const int dev = handles[0] ? handles[0]->device : -1;
   for (int i = 0; i < n; ++i) {
@@ -2097,25 +2106,32 @@ int fredopt_batch_create(fredopt_batch_t* out, const fredopt_t* handles, int n) 
     if ((e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming)) != cudaSuccess) return bad(e);
     if ((e = cudaStreamSynchronize(handles[i]->stream)) != cudaSuccess) return bad(e);
   }
-  // one iteration of every plan as parallel branches of one graph
-  if ((e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return bad(e);
-  cudaEventRecord(b->fork, b->root);
-  for (int i = 0; i < n; ++i) {
-    fredopt_t h = handles[i];
-    cudaStreamWaitEvent(h->stream, b->fork, 0);
-    const int64_t before = h->launches;
-    enqueue_iteration(h);
-    b->nodes.push_back((int)(h->launches - before));
-    h->launches = before;
-    cudaEventRecord(b->joins[i], h->stream);
-    cudaStreamWaitEvent(b->root, b->joins[i], 0);
-  }
-  e = cudaStreamEndCapture(b->root, &b->graph);
-  if (e != cudaSuccess) {
-    b->graph = nullptr;
-    return bad(e);
-  }
-  if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return bad(e);
+  // `iters` iterations of every plan as parallel branches of one graph (each
+  // branch runs its plan's iterations in order, exactly as alone)
+  auto capture = [&](int iters, cudaGraph_t* g, cudaGraphExec_t* x) -> cudaError_t {
+    cudaError_t ce = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return ce;
+    cudaEventRecord(b->fork, b->root);
+    for (int i = 0; i < n; ++i) {
+      fredopt_t h = handles[i];
+      cudaStreamWaitEvent(h->stream, b->fork, 0);
+      const int64_t before = h->launches;
+      for (int k = 0; k < iters; ++k) enqueue_iteration(h);
+      if (iters == 1) b->nodes.push_back((int)(h->launches - before));
+      h->launches = before;
+      cudaEventRecord(b->joins[i], h->stream);
+      cudaStreamWaitEvent(b->root, b->joins[i], 0);
+    }
+    ce = cudaStreamEndCapture(b->root, g);
+    if (ce != cudaSuccess) {
+      *g = nullptr;
+      return ce;
+    }
+    return cudaGraphInstantiate(x, *g, 0);
+  };
+  if ((e = capture(1, &b->graph, &b->exec)) != cudaSuccess) return bad(e);
+  b->depth = depth;
+  if (depth > 1 && (e = capture(depth, &b->graph_k, &b->exec_k)) != cudaSuccess) return bad(e);
   *out = b;
   return FREDOPT_OK;
 }
@@ -2135,7 +2151,14 @@ int fredopt_batch_iterate(fredopt_batch_t b, int iters) {
     cudaStreamWaitEvent(b->root, h->ev_join, 0);
   }
   cudaEventRecord(b->t0, b->root);
-  for (int i = 0; i < iters; ++i)
+  // whole graphs of `depth` iterations, then single iterations
+  const int nk = b->exec_k ? iters / b->depth : 0;
+  for (int i = 0; i < nk; ++i)
+    if (cudaGraphLaunch(b->exec_k, b->root) != cudaSuccess) {
+      cudaGetLastError();
+      return FREDOPT_ERR_CUDA;
+    }
+  for (int i = nk * b->depth; i < iters; ++i)
     if (cudaGraphLaunch(b->exec, b->root) != cudaSuccess) {
       cudaGetLastError();
       return FREDOPT_ERR_CUDA;
@@ -2194,7 +2217,7 @@ int fredopt_superiorize_batch(const fredopt_t* handles, int n, const float* cons
     if (rc) return rc;
   }
   fredopt_batch_t b = nullptr;
-  int rc = fredopt_batch_create(&b, handles, n);
+  int rc = fredopt_batch_create_depth(&b, handles, n, std::max(1, std::min(iters, FREDOPT_BATCH_DEPTH)));
   if (rc) return rc;
   rc = fredopt_batch_iterate(b, iters);
   if (!rc) rc = fredopt_batch_sync(b, nullptr);

@@ -176,6 +176,8 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int64)]),
     "fredopt_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                             ctypes.c_int]),
+    "fredopt_batch_create_depth": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                                  ctypes.c_int, ctypes.c_int]),
     "fredopt_batch_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fredopt_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "fredopt_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -666,15 +668,15 @@ class Server:
 
 
 class Batch:
-    """Iterations of several begun plans as one CUDA graph per iteration
-    (fredopt_batch_*)."""
+    """Iterations of several begun plans as CUDA graphs of one iteration, or
+    of `depth` iterations, of every plan (fredopt_batch_*)."""
 
-    def __init__(self, handles):
+    def __init__(self, handles, depth: int = 1):
         self.lib = load_library()
         self.handles = list(handles)
         arr = (ctypes.c_void_p * len(self.handles))(*[h.h for h in self.handles])
         b = ctypes.c_void_p()
-        rc = self.lib.fredopt_batch_create(ctypes.byref(b), arr, len(self.handles))
+        rc = self.lib.fredopt_batch_create_depth(ctypes.byref(b), arr, len(self.handles), int(depth))
         if rc != OK:
             raise FredoptError(rc, self.lib.fredopt_strerror(rc).decode())
         self.b = b

@@ -70,9 +70,54 @@ def test_bench_imports_and_serving_helpers():
     t1 = bench.serving_trace(lib, 50, 2.0, seed=5)
     t2 = bench.serving_trace(lib, 50, 2.0, seed=5)
     assert t1 == t2
-    assert all(100 <= r["iters"] <= 500 and r["fmt"] in ("fp32", "bf16") for r in t1)
+    assert all(100 <= r["iters"] <= 500 and r["fmt"] in ("fp32", "fp16") for r in t1)
+    assert {r["fmt"] for r in bench.serving_trace(lib, 50, 2.0, seed=5, fmt16="bf16")} == {"fp32", "bf16"}
     assert np.all(np.diff([r["t"] for r in t1]) > 0)
     res = [({"t_submit": float(i), "t_done": float(i) + 1.0 + (i == 9), "status": 3},) for i in range(10)]
     s = bench.serving_summary(res, 10)
     assert s["all_done"] and s["p50_latency_s"] == 1.0 and s["makespan_s"] == 11.0
     assert s["plans_per_hour"] == 10 / 11.0 * 3600
+
+
+def test_row_sample_config_and_byte_models():
+    """The reference arm's row sample keeps every m-th voxel row bit for bit;
+    both arms print the same config for the same plan; the int32 accounting
+    counts 12 + 2 vb bytes per nonzero."""
+    import numpy as np
+    import bench
+    import phantom
+    pl = phantom.tiny_plan()
+    sub = bench.row_sample(pl, 7)
+    rows = np.arange(0, pl.n_vox, 7)
+    assert sub.n_vox == len(rows) and sub.n_spots == pl.n_spots
+    np.testing.assert_array_equal(sub.mask, pl.mask[rows])
+    for i in (0, 5, len(rows) - 1):
+        r = rows[i]
+        s0, s1 = pl.row_ptr[r], pl.row_ptr[r + 1]
+        np.testing.assert_array_equal(sub.col[sub.row_ptr[i]:sub.row_ptr[i + 1]], pl.col[s0:s1])
+        np.testing.assert_array_equal(sub.D[sub.row_ptr[i]:sub.row_ptr[i + 1]], pl.D[s0:s1])
+    assert bench.workload_config(10, 3, 100, "fp32", 1) == bench.workload_config(10, 3, 100, "fp32", 1)
+    assert bench.pass_bytes_int32(1000, 10, 3, 4) == 1000 * 12 + 10 * 12 + 12
+    assert bench.pass_bytes_int32(1000, 10, 3, 2) == 1000 * 8 + 10 * 20 + 12
+    info = bench.cpu_info()
+    assert info["nproc"] >= 1 and "cpu_model" in info
+
+
+def test_output_errors_against_the_oracle():
+    """The CPU leg's error measure: zero for the oracle's own outputs, the
+    dose error in units of the prescription, LETd only above 1% of it."""
+    import numpy as np
+    import bench
+    import oracle
+    import phantom
+    pl = phantom.tiny_plan()
+    P = oracle.build_problem(pl.row_ptr, pl.col, pl.D, pl.L, pl.n_spots, pl.mask, pl.constraints, pl.objective)
+    w = pl.w0.astype(np.float64)
+    d, l = oracle.forward(P, w)
+    let = oracle.letd(d, l)
+    e = bench.output_errors(P, w, d, let, 2.0)
+    assert e["dose_max_frac_of_presc"] == 0.0 and e["letd_max_keV_um"] == 0.0
+    d2 = d.copy()
+    d2[np.argmax(d)] += 0.002
+    e = bench.output_errors(P, w, d2, let, 2.0)
+    assert e["dose_max_frac_of_presc"] == pytest.approx(0.001)

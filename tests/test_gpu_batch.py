@@ -1,6 +1,6 @@
-"""Batches of plans (one CUDA graph per iteration for all plans) and tile
-autotuning: results are bit-identical to running each plan alone with the
-default tiles."""
+"""Batches of plans (CUDA graphs of one or several iterations of all plans)
+and tile autotuning: results are bit-identical to running each plan alone
+with the default tiles."""
 import numpy as np
 import pytest
 
@@ -61,15 +61,19 @@ def test_batch_matches_each_plan_alone(lib):
         np.testing.assert_array_equal(w, wr)
         np.testing.assert_array_equal(d, dr)
         assert rep["iters"] == iters
-    # the explicit form, continued in two pieces, then finished per plan
-    for h, (p, f) in zip(hs, specs):
-        h.begin(p.w0, 0.99, 1.0, use_graphs=0)
-    with lib.Batch(hs) as b:
-        b.iterate(10)
-        b.iterate(iters - 10)
-        ms = b.sync()
-    assert ms > 0
-    for h, (wr, dr, lr, rr) in zip(hs, refs):
-        w, d, l, rep = h.end()
-        np.testing.assert_array_equal(w, wr)
+    # the explicit form, continued in two pieces, then finished per plan;
+    # graphs of one iteration and of 4 iterations of every plan
+    for depth in (1, 4):
+        for h, (p, f) in zip(hs, specs):
+            h.begin(p.w0, 0.99, 1.0, use_graphs=0)
+        with lib.Batch(hs, depth=depth) as b:
+            b.iterate(10)
+            b.iterate(iters - 10)
+            ms = b.sync()
+        assert ms > 0
+        for h, (wr, dr, lr, rr) in zip(hs, refs):
+            w, d, l, rep = h.end()
+            np.testing.assert_array_equal(w, wr)
+            assert rep["iters"] == iters
+    for h in hs:
         h.close()
