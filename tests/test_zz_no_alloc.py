@@ -122,7 +122,7 @@ def test_multi_chunk_columns_and_empty_columns(env, with_aD):
 
 def test_largest_column_count(env):
     """65536 columns, the most the scratch's offset table holds."""
-    n_rows = 5000
+    n_rows = 12000
     rng = np.random.default_rng(5)
     lens = rng.integers(0, 40, MAX_COLS)
     lens[[0, 777, MAX_COLS - 1]] = [9000, 4097, 5000]   # a few multi-chunk columns
