@@ -134,7 +134,7 @@ class ClockSampler:
 FWD_TRAFFIC_PER_NNZ = {("fp32", 4): 12.48, ("fp32", 2): 10.17}
 # the same for the transposed product (average of its gradient and projection
 # launches), keyed by (storage, row index bytes)
-BWD_TRAFFIC_PER_NNZ = {("fp32", 2): 8.26}
+BWD_TRAFFIC_PER_NNZ = {("fp32", 2): 8.28, ("bf16", 2): 5.23}
 
 
 def fwd_bytes(nnz, rows, vb, ib, n_launch_obj, n_launch_bc):
