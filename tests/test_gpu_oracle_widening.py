@@ -175,3 +175,43 @@ def test_served_requests_vs_oracle(lib):
         assert info["status"] == lib.DONE
         P, R, w_ref, log_ref = oracle_run(lib, p, f, ITERS)
         assert_matches_oracle(p, P, w_ref, log_ref, w, dose, report=info["report"])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_16bit_sweep_vs_oracle(lib, fmt):
+    """The block-iterative sweep (R13) with 16-bit storage: one sweep of 37
+    blocks from the same x within 2e-5 relative L2 of the oracle's sweep on
+    the stored values, and 15 superiorized iterations with a 16-block sweep
+    as the feasibility operator matching the oracle's trial counters and w."""
+    plan = phantom.tiny_plan()
+    rp, col, D, L = stored_matrix(lib, plan, fmt)
+    P = oracle.build_problem(rp, col, D, L, plan.n_spots, plan.mask, plan.constraints, plan.objective)
+    R = oracle.constraint_rows(P)
+    x = np.random.default_rng(37).uniform(0.2, 2.5, plan.n_spots).astype(np.float32)
+    ref = oracle.block_iterative_sweep(R, x.astype(np.float64), 1.0, oracle.sweep_blocks(P, R, 37), prio_scale=0.8)
+    w_ref, log_ref = oracle.superiorize(P, plan.w0, 15, plan.alpha, plan.relaxation, rows=R, sweep=16)
+    with lib.Handle(0) as h:
+        h.load_plan(plan, fmt=fmt)
+        sw = h.sweep_step(x, 37, relaxation=1.0, prio_scale=0.8)
+        w, dose, letd, rep = h.superiorize(plan.w0, 15, plan.alpha, plan.relaxation, sweep_blocks=16)
+        log = h.get_log()
+    assert np.linalg.norm(sw - ref) / np.linalg.norm(ref) <= 2e-5
+    assert [e["s"] for e in log] == [e["s"] for e in log_ref]
+    assert np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_16bit_quantity_maps_vs_oracle(lib, fmt):
+    """Dose, cDL and LETd maps of 16-bit storage (the double-float final pass
+    over the stored values, rounded once to FP32) within 1e-6 relative of the
+    oracle's FP64 maps of the stored matrix."""
+    plan = phantom.tiny_plan()
+    rp, col, D, L = stored_matrix(lib, plan, fmt)
+    P = oracle.build_problem(rp, col, D, L, plan.n_spots, plan.mask, plan.constraints, plan.objective)
+    w = np.random.default_rng(12).uniform(0.0, 2.0, plan.n_spots).astype(np.float32)
+    with lib.Handle(0) as h:
+        h.load_plan(plan, fmt=fmt)
+        maps = {q: h.quantity_map(w, q) for q in ("DOSE", "CDL", "LETD")}
+    for q, name in (("DOSE", "dose"), ("CDL", "cdl"), ("LETD", "letd")):
+        ref = oracle.quantity(P, w, name)
+        assert np.all(np.abs(maps[q] - ref) <= 1e-6 * np.abs(ref) + 1e-12), q
