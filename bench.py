@@ -131,10 +131,10 @@ class ClockSampler:
 # two forward launches of an iteration), keyed by (storage, index bytes);
 # traffic grows with the nonzeros, so it is scaled to the full plan.  A
 # stream without a capture reports null.
-FWD_TRAFFIC_PER_NNZ = {("fp32", 4): 12.48, ("fp32", 2): 10.17}
+FWD_TRAFFIC_PER_NNZ = {("fp32", 4): 12.48, ("fp32", 2): 10.17, ("bf16", 2): 6.18, ("fp16", 2): 6.18}
 # the same for the transposed product (average of its gradient and projection
 # launches), keyed by (storage, row index bytes)
-BWD_TRAFFIC_PER_NNZ = {("fp32", 2): 8.28, ("bf16", 2): 5.23}
+BWD_TRAFFIC_PER_NNZ = {("fp32", 2): 8.28, ("bf16", 2): 5.23, ("fp16", 2): 5.23}
 
 
 def fwd_bytes(nnz, rows, vb, ib, n_launch_obj, n_launch_bc):
