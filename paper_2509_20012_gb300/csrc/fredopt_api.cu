@@ -103,6 +103,10 @@ struct fredopt_ctx {
   std::vector<int64_t> h_cptr;   // chunk_ptr (host copy)
   int64_t row_cost = 0, chunk_cost = 0;  // warp-partition weights in use
   std::vector<uint32_t> h_mask;  // per streamed row
+  DBuf<int64_t> con_rows;        // streamed rows with a structure bit, ascending
+  std::vector<int64_t> h_con_rows;
+  int64_t n_con_rows = 0;
+  DBuf<float2> ucoef;            // coefficients of fredopt_backward (kept apart from gam)
 
   // problem
   Tables tab{};
@@ -423,6 +427,8 @@ ConArgs con_args(fredopt_t h) {
   c.sD = h->fmt ? h->sD.p : nullptr;
   c.sL = h->fmt ? h->sL.p : nullptr;
   c.n_hot = h->n_hot;
+  c.rows = h->con_rows.p;
+  c.n_list = h->n_con_rows;
   c.gam = h->gam.p;
   c.part = h->part.p + h->off_k2;
   c.st = h->st.p;
@@ -497,6 +503,7 @@ void enqueue_sweep(fredopt_t h, const float* w, int use_coef, double lam, double
     k2.yw = h->ys.p;
     k2.yg = nullptr;
     k2.use_coef = 0;
+    k2.rows = nullptr;  // the block's row range
     k2.r0 = h->h_sweep_bounds[t];
     k2.n_hot = h->h_sweep_bounds[t + 1];
     // one CTA per 256 rows of the block, at most the usual grid
@@ -968,7 +975,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
 
   // ---- drop the previous plan
   h->rp.release(); h->col.release(); h->col16.release(); h->Dv.release(); h->Lv.release(); h->sD.release(); h->sL.release();
-  h->voxel.release(); h->mask.release(); h->cp.release(); h->crow.release(); h->crow16.release(); h->chdr.release(); h->covf.release(); h->DTv.release(); h->LTv.release();
+  h->voxel.release(); h->mask.release(); h->con_rows.release(); h->ucoef.release(); h->cp.release(); h->crow.release(); h->crow16.release(); h->chdr.release(); h->covf.release(); h->DTv.release(); h->LTv.release();
 
   // ---- FP32 CSR in device order (zero padded)
   DBuf<int32_t> col_d;
@@ -1028,6 +1035,16 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   h->h_mask.resize(n_hot);
   for (int64_t r = 0; r < n_hot; ++r) h->h_mask[r] = m0[order[r]];
   CK(upload_vec(h, h->mask, h->h_mask));
+  {
+    // the constraint evaluation visits only these rows; the others' projection
+    // coefficients stay 0
+    std::vector<int64_t>& cr = h->h_con_rows;
+    cr.clear();
+    for (int64_t r = 0; r < n_hot; ++r)
+      if (h->h_mask[r] != 0) cr.push_back(r);
+    h->n_con_rows = (int64_t)cr.size();
+    CK(upload_vec(h, h->con_rows, cr));
+  }
   CK(h->mdd.alloc(n_hot)); CK(h->mll.alloc(n_hot)); CK(h->mdl.alloc(n_hot));
   CK(cudaMemsetAsync(h->mdd.p, 0, std::max<int64_t>(1, n_hot) * sizeof(double), s));
   CK(cudaMemsetAsync(h->mll.p, 0, std::max<int64_t>(1, n_hot) * sizeof(double), s));
@@ -1167,6 +1184,8 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   CK(cudaMemsetAsync(h->yw.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
   CK(cudaMemsetAsync(h->yg.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
   CK(cudaMemsetAsync(h->r.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
+  // projection coefficients: rows without a structure bit are never written
+  CK(cudaMemsetAsync(h->gam.p, 0, std::max<int64_t>(1, n_hot) * sizeof(float2), s));
   CK(h->chunk_sum.alloc(h->n_chunks));
   const Geometry& G = h->geo;
   // forward partials: one per tile (at most 7 guided tiles per warp)
@@ -1567,9 +1586,10 @@ int fredopt_backward(fredopt_t h, const float* a_D, const float* a_L, float* u_o
     pa = a_D ? h->vin_a.p : nullptr;
     pb = a_L ? h->vin_b.p : nullptr;
   }
+  CK(h->ucoef.ensure(std::max<int64_t>(1, h->n_hot)));
   launch_scale_coef(h->n_hot, pa, pb, h->perm ? h->voxel.p : nullptr, h->fmt ? h->sD.p : nullptr,
-                    h->fmt ? h->sL.p : nullptr, h->gam.p, s);
-  BwdArgs ba = bwd_args(h, h->gam.p);
+                    h->fmt ? h->sL.p : nullptr, h->ucoef.p, s);
+  BwdArgs ba = bwd_args(h, h->ucoef.p);
   run(h, 1, [&] { launch_backward(h->geo, h->fmt, h->hint_bwd, true, ba, s); });
   ColArgs ca = col_args(h);
   ca.out = h->gtmp.p;

@@ -160,6 +160,10 @@ struct ConArgs {
   const float* sL;
   int64_t r0;           // rows [r0, n_hot) are evaluated (0 for the whole set)
   int64_t n_hot;
+  // when set, the rows evaluated are rows[0 .. n_list) instead (the rows
+  // with a structure bit, ascending); every other row's gam stays 0
+  const int64_t* rows;
+  int64_t n_list;
   float2* gam;
   double* part;         // per-block: [sum p violated, n violated, max violation, sum p reachable]
   int32_t use_coef;

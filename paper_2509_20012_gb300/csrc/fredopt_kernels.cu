@@ -852,8 +852,11 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     float s = 0.0f;
     if (a.use_u) {
+      // the chunk sums of the column in chunk order (loads unrolled ahead of
+      // the sequential additions)
       const int c1 = a.col_chunk[j + 1];
-      for (int c = a.col_chunk[j]; c < c1; ++c) s += a.chunk_sum[c];
+#pragma unroll 8
+      for (int c = a.col_chunk[j]; c < c1; ++c) s += __ldcg(&a.chunk_sum[c]);
     }
     if (MODE == COL_OUT) {
       a.out[j] = s;
@@ -909,13 +912,16 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
 // ------------------------------------------------------------------ K2
 
 __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t) {
-  __shared__ double red[kRowThreads];
-  const int64_t per = (a.n_hot - a.r0 + gridDim.x - 1) / gridDim.x;
-  const int64_t i0 = a.r0 + (int64_t)blockIdx.x * per;
-  const int64_t i1 = min(a.n_hot, i0 + per);
+  // block b evaluates a contiguous slice of the rows: of [r0, n_hot), or of
+  // the listed rows
+  const int64_t lo = a.rows ? 0 : a.r0, hi = a.rows ? a.n_list : a.n_hot;
+  const int64_t per = (hi - lo + gridDim.x - 1) / gridDim.x;
+  const int64_t j0 = lo + (int64_t)blockIdx.x * per;
+  const int64_t j1 = min(hi, j0 + per);
   const double coef = a.use_coef ? a.st->coef : 0.0;
   double psum = 0.0, nv = 0.0, mx = 0.0, preach = 0.0;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const int64_t i = a.rows ? a.rows[j] : j;
     const uint32_t m = a.mask[i];
     float2 out = make_float2(0.f, 0.f);
     if (m) {
@@ -962,15 +968,29 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
     }
     a.gam[i] = out;
   }
-  psum = block_sum256(psum, red);
-  nv = block_sum256(nv, red);
-  mx = block_max256(mx, red);
-  preach = block_sum256(preach, red);
+  // the block's three sums and its maximum in one fixed tree (each in the
+  // order of block_sum256 / block_max256)
+  __shared__ double red4[4][kRowThreads];
+  red4[0][threadIdx.x] = psum;
+  red4[1][threadIdx.x] = nv;
+  red4[2][threadIdx.x] = mx;
+  red4[3][threadIdx.x] = preach;
+  __syncthreads();
+#pragma unroll
+  for (int o = kRowThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red4[0][threadIdx.x] += red4[0][threadIdx.x + o];
+      red4[1][threadIdx.x] += red4[1][threadIdx.x + o];
+      red4[2][threadIdx.x] = fmax(red4[2][threadIdx.x], red4[2][threadIdx.x + o]);
+      red4[3][threadIdx.x] += red4[3][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    a.part[blockIdx.x] = psum;
-    a.part[gridDim.x + blockIdx.x] = nv;
-    a.part[2 * gridDim.x + blockIdx.x] = mx;
-    a.part[3 * gridDim.x + blockIdx.x] = preach;
+    a.part[blockIdx.x] = red4[0][0];
+    a.part[gridDim.x + blockIdx.x] = red4[1][0];
+    a.part[2 * gridDim.x + blockIdx.x] = red4[2][0];
+    a.part[3 * gridDim.x + blockIdx.x] = red4[3][0];
   }
 }
 
@@ -984,37 +1004,101 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
                                                 const double* part_bc, int nbc, const double* part_g,
                                                 int ng, DevState* st, double* stage) {
   __shared__ double red[256];
+  __shared__ double red4[4][256];
+  __shared__ double sh_beta;
   __shared__ bool sh_last;
   const int G = gridDim.x, b = blockIdx.x;
-  auto slice_sum = [&](const double* p, int n) {
-    const int per = (n + G - 1) / G;
-    const int i0 = min(n, b * per), i1 = min(n, i0 + per);
-    return block_sum_array(p + i0, i1 - i0, red);
-  };
-  const double f1 = slice_sum(part_f, nf);
-  const double b1 = slice_sum(part_bc, nbc);
-  const double c1 = slice_sum(part_bc + nbc, nbc);
-  const double g1 = slice_sum(part_g, ng);
+  // the four sums of this block's slices at once: per thread a strided sum,
+  // then one fixed tree for all four (the order of each sum is that of
+  // block_sum_array)
+  {
+    const double* arr[4] = {part_f, part_bc, part_bc + nbc, part_g};
+    const int len[4] = {nf, nbc, nbc, ng};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int per = (len[k] + G - 1) / G;
+      const int i0 = min(len[k], b * per), i1 = min(len[k], i0 + per);
+      double v = 0.0;
+      for (int i = i0 + threadIdx.x; i < i1; i += 256) v += arr[k][i];
+      red4[k][threadIdx.x] = v;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red4[k][threadIdx.x] += red4[k][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    stage[b] = f1;
-    stage[G + b] = b1;
-    stage[2 * G + b] = c1;
-    stage[3 * G + b] = g1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) stage[k * G + b] = red4[k][0];
     __threadfence();
     sh_last = atomicAdd(&st->done_fin, 1u) == (unsigned)G - 1;
   }
   __syncthreads();
   if (!sh_last) return;
   __threadfence();
-  auto stage_sum = [&](int k) {  // written by other CTAs of this launch: read past L1
+  // the slice sums, written by other CTAs of this launch: read past L1
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
     double v = 0.0;
     for (int i = threadIdx.x; i < G; i += 256) v += __ldcg(&stage[k * G + i]);
-    return block_sum256(v, red);
-  };
-  const double f = stage_sum(0) + (step == 0 ? st->f_empty : 0.0);
-  const double Bp = stage_sum(1);
-  const double Cp = stage_sum(2);
-  const double gn2 = stage_sum(3);
+    red4[k][threadIdx.x] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red4[k][threadIdx.x] += red4[k][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const double f = red4[0][0] + (step == 0 ? st->f_empty : 0.0);
+  const double Bp = red4[1][0];
+  const double Cp = red4[2][0];
+  const double gn2 = red4[3][0];
+  // The trial loop of Fig. 3 (beta = beta0 alpha^s, s advancing on every
+  // trial, accept the first trial that does not ascend, at most max_trials):
+  // the block evaluates consecutive trials at once, each thread one, and
+  // takes the first accepted one (a block minimum of the trial index), so
+  // the decision and s are those of the trials taken in turn.  The first
+  // round tries 8 trials (most iterations accept one of them; each trial
+  // costs an FP64 pow, slow on GB300), later rounds 256.
+  const long long s0 = st->s;
+  const int max_trials = st->max_trials;
+  const double gn = gn2 > 0.0 ? sqrt(gn2) : 0.0;
+  double B = 0.0, C = 0.0;
+  if (gn2 > 0.0) {
+    if (st->grad_normalize) { B = -Bp / gn; C = Cp / gn2; }
+    else { B = -Bp; C = Cp; }
+  }
+  int first = max_trials;  // index of the accepted trial, max_trials if none
+  if (gn2 > 0.0) {
+    for (int base = 0, width = 8; base < max_trials && first == max_trials; base += width, width = 256) {
+      const int tr = base + (int)threadIdx.x;
+      double cand = (double)max_trials;
+      double beta = 0.0;
+      if ((int)threadIdx.x < width && tr < max_trials) {
+        beta = st->beta0 * pow(st->alpha, (double)(s0 + tr));
+        const double df = beta * (2.0 * B + beta * C);  // f(x + beta v) - f(x), Eq. 2 is quadratic
+        if (df <= 0.0) cand = (double)tr;
+      }
+      red[threadIdx.x] = cand;
+      __syncthreads();
+#pragma unroll
+      for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+      }
+      first = (int)red[0];
+      if (tr == first) sh_beta = beta;  // the accepted trial's step
+      __syncthreads();
+    }
+  }
   if (threadIdx.x != 0) return;
   st->done_fin = 0u;
   if (step == 0) {
@@ -1024,25 +1108,19 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   }
   double fc = f;
   double coef = 0.0;
-  long long s = st->s;
+  long long s = s0;
   if (gn2 > 0.0) {
-    const double gn = sqrt(gn2);
     st->gnorm = gn;
-    double B, C;
-    if (st->grad_normalize) { B = -Bp / gn; C = Cp / gn2; }
-    else { B = -Bp; C = Cp; }
-    for (int tr = 0; tr < st->max_trials; ++tr) {
-      const double beta = st->beta0 * pow(st->alpha, (double)s);
-      s += 1;
-      const double df = beta * (2.0 * B + beta * C);  // f(x + beta v) - f(x), Eq. 2 is quadratic
-      if (df <= 0.0) {
-        coef = st->grad_normalize ? -beta / gn : -beta;
-        st->accepted += 1;
-        st->accepted_total += 1;
-        st->beta_acc = beta;
-        fc = f + df;
-        break;
-      }
+    if (first < max_trials) {
+      const double beta = sh_beta;
+      coef = st->grad_normalize ? -beta / gn : -beta;
+      st->accepted += 1;
+      st->accepted_total += 1;
+      st->beta_acc = beta;
+      fc = f + beta * (2.0 * B + beta * C);
+      s = s0 + first + 1;
+    } else {
+      s = s0 + max_trials;
     }
   } else {
     st->gnorm = 0.0;
