@@ -121,3 +121,31 @@ def test_output_errors_against_the_oracle():
     d2[np.argmax(d)] += 0.002
     e = bench.output_errors(P, w, d2, let, 2.0)
     assert e["dose_max_frac_of_presc"] == pytest.approx(0.001)
+
+
+def test_serving_accuracy_bar():
+    """The serving check compares each served plan's solution with the FP32
+    result of the same request through the oracle's FP64 products: equal
+    weights pass, a dose difference above 1e-4 of the prescription fails."""
+    import numpy as np
+    import bench
+    from concurrent.futures import ThreadPoolExecutor
+    import phantom
+    pl = phantom.tiny_plan()
+    w = np.random.default_rng(4).uniform(0.5, 1.5, pl.n_spots).astype(np.float32)
+    trace = [dict(t=0.0, plan=0, fmt="fp32", iters=100), dict(t=0.5, plan=0, fmt="fp16", iters=100)]
+    import oracle
+    P = oracle.build_problem(pl.row_ptr, pl.col, pl.D, pl.L, pl.n_spots, pl.mask, pl.constraints, pl.objective)
+    d, l = oracle.forward(P, w.astype(np.float64))
+    let = oracle.letd(d, l).astype(np.float32)
+    serving = {"lib": [pl], "trace": trace, "served_w": [w, w.copy()], "seq_w": [w, w.copy()],
+               "served_dose": [d.astype(np.float32)] * 2, "served_letd": [let] * 2}
+    with ThreadPoolExecutor(2) as pool:
+        ok = bench.serving_accuracy(serving, None, None, 2, pool)
+        assert ok["accuracy_ok"] and len(ok["requests"]) == 2
+        assert ok["worst_by_format"]["fp16"]["solution_dose_max_frac_of_presc"] == 0.0
+        w2 = (w * 1.01).astype(np.float32)        # a 1% different plan: about 1e-2 of the prescription
+        serving["served_w"] = [w, w2]
+        bad = bench.serving_accuracy(serving, None, None, 2, pool)
+    assert not bad["accuracy_ok"]
+    assert bad["worst_by_format"]["fp16"]["solution_dose_max_frac_of_presc"] > 1e-3
