@@ -1197,7 +1197,7 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   h->off_fin = h->off_k2 + 4 * G.row_blocks;
   h->off_cnt = h->off_fin + 8 * G.row_blocks;
   h->off_stage = h->off_cnt + 3 * G.row_blocks;
-  h->n_part = h->off_stage + 4 * kFinishBlocks;
+  h->n_part = h->off_stage + 5 * kFinishBlocks;
   CK(h->part.alloc(h->n_part));
   CK(cudaMemsetAsync(h->part.p, 0, h->n_part * sizeof(double), s));
   h->y64.release(); h->yall.release(); h->fout_a.release(); h->fout_b.release();

@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
     double W = a.W_all;
     if (a.norm == 1) W = block_sum_array(a.k2part, a.k2_blocks, red);
     if (threadIdx.x == 0) {
-      const double ps = a.in_solve ? pow(a.st->eta, (double)a.st->k) : a.prio_scale;
+      const double ps = a.in_solve ? (a.st->eta == 1.0 ? 1.0 : pow(a.st->eta, (double)a.st->k)) : a.prio_scale;
       sh_scale = W > 0.0 ? a.lam * ps / W : 0.0;
     }
     __syncthreads();
@@ -1035,6 +1035,9 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) stage[k * G + b] = red4[k][0];
+    // the step of trial b of this iteration, ready for the last block (the
+    // pow, slow in FP64, overlaps the other blocks' sums)
+    stage[4 * G + b] = st->beta0 * pow(st->alpha, (double)(st->s + b));
     __threadfence();
     sh_last = atomicAdd(&st->done_fin, 1u) == (unsigned)G - 1;
   }
@@ -1065,9 +1068,9 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   // trial, accept the first trial that does not ascend, at most max_trials):
   // the block evaluates consecutive trials at once, each thread one, and
   // takes the first accepted one (a block minimum of the trial index), so
-  // the decision and s are those of the trials taken in turn.  The first
-  // round tries 8 trials (most iterations accept one of them; each trial
-  // costs an FP64 pow, slow on GB300), later rounds 256.
+  // the decision and s are those of the trials taken in turn.  The steps of
+  // the first 64 trials were computed by the 64 blocks; later rounds of 256
+  // trials compute their own (an FP64 pow each, slow on GB300).
   const long long s0 = st->s;
   const int max_trials = st->max_trials;
   const double gn = gn2 > 0.0 ? sqrt(gn2) : 0.0;
@@ -1078,12 +1081,12 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   }
   int first = max_trials;  // index of the accepted trial, max_trials if none
   if (gn2 > 0.0) {
-    for (int base = 0, width = 8; base < max_trials && first == max_trials; base += width, width = 256) {
+    for (int base = 0, width = 64; base < max_trials && first == max_trials; base += width, width = 256) {
       const int tr = base + (int)threadIdx.x;
       double cand = (double)max_trials;
       double beta = 0.0;
       if ((int)threadIdx.x < width && tr < max_trials) {
-        beta = st->beta0 * pow(st->alpha, (double)(s0 + tr));
+        beta = tr < G ? __ldcg(&stage[4 * G + tr]) : st->beta0 * pow(st->alpha, (double)(s0 + tr));
         const double df = beta * (2.0 * B + beta * C);  // f(x + beta v) - f(x), Eq. 2 is quadratic
         if (df <= 0.0) cand = (double)tr;
       }
@@ -1944,7 +1947,7 @@ __global__ void __launch_bounds__(256) k_sweep_update(SweepArgs a) {
     }
   }
   if (threadIdx.x == 0) {
-    const double ps = a.in_solve ? pow(a.st->eta, (double)a.st->k) : a.prio_scale;
+    const double ps = a.in_solve ? (a.st->eta == 1.0 ? 1.0 : pow(a.st->eta, (double)a.st->k)) : a.prio_scale;
     sh_scale = W > 0.0 ? a.lam * ps / W : 0.0;
   }
   __syncthreads();
