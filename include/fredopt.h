@@ -347,7 +347,12 @@ int fredopt_get_moments(fredopt_t h, double* dd, double* ll, double* dl);
 /* Device time (ms, CUDA events on the handle's stream) and launch count of
  * each kernel class since the last reset, when timing is enabled.  Classes:
  * 0 forward product, 1 transposed product, 2 constraint evaluation,
- * 3 column finish, 4 scalar finish, 5 other. */
+ * 3 column finish, 4 scalar finish, 5 other.  With timing enabled at
+ * fredopt_begin and use_graphs = 1, the iteration graph holds an event-record
+ * node before and after each kernel and every replay points them at fresh
+ * events, so the kernels run as graph replays and are still timed one by
+ * one.  Timing switched on or off after fredopt_begin runs the iterations as
+ * plain launches (timed or not) until the next fredopt_begin. */
 #define FREDOPT_KCLASS_N 6
 int fredopt_set_timing(fredopt_t h, int enable);
 int fredopt_get_timing(fredopt_t h, double* ms, int64_t* launches);

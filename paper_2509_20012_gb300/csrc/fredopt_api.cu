@@ -52,6 +52,12 @@ struct Timer {
   int cls = 0;
 };
 
+// the two event-record nodes around one kernel of a timed iteration graph
+struct GraphTimer {
+  cudaGraphNode_t a = nullptr, b = nullptr;
+  int cls = 0;
+};
+
 }  // namespace
 
 struct fredopt_ctx {
@@ -153,6 +159,9 @@ struct fredopt_ctx {
   bool timing = false;
   std::vector<Timer> timers;
   size_t timers_used = 0;
+  bool capturing = false;            // enqueue_iteration is being captured into `graph`
+  bool graph_timed = false;          // `graph` holds an event pair around each kernel
+  std::vector<GraphTimer> gtimers;   // those pairs, in kernel order
   double kms[FREDOPT_KCLASS_N] = {0};
   int64_t klaunch[FREDOPT_KCLASS_N] = {0};
   int64_t launches = 0;  // kernels enqueued (graph replays count their nodes)
@@ -308,23 +317,33 @@ void free_graph(fredopt_t h) {
   h->gexec = nullptr;
   h->graph = nullptr;
   h->graph_nodes = 0;
+  h->graph_timed = false;
+  h->gtimers.clear();
 }
 
 // ---- timed launch helper ----
+Timer& next_timer(fredopt_t h, int cls) {
+  if (h->timers_used == h->timers.size()) {
+    Timer t;
+    cudaEventCreate(&t.a);
+    cudaEventCreate(&t.b);
+    h->timers.push_back(t);
+  }
+  Timer& t = h->timers[h->timers_used++];
+  t.cls = cls;
+  return t;
+}
+
 template <class F>
 void run(fredopt_t h, int cls, F&& f) {
   if (h->timing) {
-    if (h->timers_used == h->timers.size()) {
-      Timer t;
-      cudaEventCreate(&t.a);
-      cudaEventCreate(&t.b);
-      h->timers.push_back(t);
-    }
-    Timer& t = h->timers[h->timers_used++];
-    t.cls = cls;
-    cudaEventRecord(t.a, h->stream);
+    Timer& t = next_timer(h, cls);
+    // under stream capture the external flag makes each record a graph node;
+    // every replay points those nodes at fresh events (fredopt_iterate)
+    const unsigned fl = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaEventRecordWithFlags(t.a, h->stream, fl);
     f();
-    cudaEventRecord(t.b, h->stream);
+    cudaEventRecordWithFlags(t.b, h->stream, fl);
   } else {
     f();
   }
@@ -1340,17 +1359,54 @@ int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
   h->iters_run = 0;
   h->device_ms = 0.0;
   h->it_pending = false;
-  if (p.use_graphs && !h->timing) {
+  if (p.use_graphs) {
     const int64_t before = h->launches;
+    const size_t t0 = h->timers_used;
+    h->capturing = true;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     enqueue_iteration(h);
     cudaError_t e = cudaStreamEndCapture(s, &h->graph);
+    h->capturing = false;
     if (e != cudaSuccess) {
       h->graph = nullptr;
+      h->timers_used = t0;
       return cuda_fail(h, e, "graph capture");
     }
     h->graph_nodes = (int)(h->launches - before);
     h->launches = before;
+    if (h->timing) {
+      // the event-record nodes of the capture, matched to the kernels' timers
+      size_t n = 0;
+      CK(cudaGraphGetNodes(h->graph, nullptr, &n));
+      std::vector<cudaGraphNode_t> nodes(n);
+      CK(cudaGraphGetNodes(h->graph, nodes.data(), &n));
+      std::vector<std::pair<cudaEvent_t, cudaGraphNode_t>> rec;
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        CK(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        rec.emplace_back(ev, nd);
+      }
+      auto node_of = [&](cudaEvent_t ev) -> cudaGraphNode_t {
+        for (auto& r : rec)
+          if (r.first == ev) return r.second;
+        return nullptr;
+      };
+      h->gtimers.clear();
+      for (size_t i = t0; i < h->timers_used; ++i) {
+        GraphTimer g{node_of(h->timers[i].a), node_of(h->timers[i].b), h->timers[i].cls};
+        if (!g.a || !g.b) {
+          h->timers_used = t0;
+          free_graph(h);
+          return fail(h, FREDOPT_ERR_CUDA, "timed graph capture: event node missing");
+        }
+        h->gtimers.push_back(g);
+      }
+      h->timers_used = t0;  // captured, not recorded: no times to collect
+      h->graph_timed = true;
+    }
     CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
   }
   CK(cudaStreamSynchronize(s));
@@ -1373,7 +1429,14 @@ int fredopt_iterate(fredopt_t h, int iters) {
   }
   CK(cudaEventRecord(h->ev_it0, h->stream));
   for (int i = 0; i < iters; ++i) {
-    if (h->gexec && !h->timing) {
+    if (h->gexec && h->graph_timed == h->timing) {
+      // a timed graph records each kernel's events into fresh timers; the
+      // update affects this and later launches only
+      for (const GraphTimer& g : h->gtimers) {
+        Timer& t = next_timer(h, g.cls);
+        CK(cudaGraphExecEventRecordNodeSetEvent(h->gexec, g.a, t.a));
+        CK(cudaGraphExecEventRecordNodeSetEvent(h->gexec, g.b, t.b));
+      }
       CK(cudaGraphLaunch(h->gexec, h->stream));
       h->launches += h->graph_nodes;
     } else {

@@ -561,21 +561,30 @@ def test_input_errors_leave_handle_usable(lib, tiny):
     np.testing.assert_array_equal(w, w_ok)
 
 
-def test_launch_count_and_timing(lib, tiny):
+@pytest.mark.parametrize("use_graphs", [1, 0])
+def test_launch_count_and_timing(lib, tiny, use_graphs):
+    """Timed iterations, as graph replays with an event pair around each
+    kernel or as plain launches: every kernel is counted and timed, and w is
+    bit-identical to an untimed graph run."""
     pl, P, R = tiny
     with handle(lib, pl) as h:
         h.set_timing(True)
-        h.begin(pl.w0, pl.alpha, pl.relaxation)
-        h.iterate(4)
-        h.end()
+        h.begin(pl.w0, pl.alpha, pl.relaxation, use_graphs=use_graphs)
+        h.iterate(1)
+        h.iterate(3)
+        w, *_ = h.end()
         t = h.get_timing()
         n = h.launch_count()
     # per iteration: 2 forward, 2 transposed, 2 column finishes, 1 scalar finish, 1 constraint kernel
     assert t["forward"][1] == 2 * 4 + 1
     assert t["backward"][1] == 2 * 4
     assert t["constraints"][1] == 4
+    assert t["finish"][1] == 4
     assert n >= 8 * 4
     assert all(ms >= 0 for ms, c in t.values())
+    assert t["forward"][0] > 0 and t["backward"][0] > 0
+    w_ref, *_ = run_gpu(lib, pl, 4)
+    np.testing.assert_array_equal(w, w_ref)
 
 
 def test_final_pass_is_fp64_product_of_fp32_inputs(lib, tiny):
