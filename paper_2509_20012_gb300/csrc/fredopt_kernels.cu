@@ -792,41 +792,99 @@ __global__ void __launch_bounds__(kBwdThreads, FO_BWD_MIN_BLOCKS) k_backward(Bwd
 
 // ------------------------------------------------------------------ block reductions
 
-// Fixed-order block reduction of one double per thread (blockDim = 256).
+// Block reductions of one double per thread (blockDim = 256), in a fixed
+// order: a warp butterfly, then thread 0 adds the 8 warp results in warp
+// order.  GB300 runs FP64 at a small fraction of its FP32 rate, and every
+// FP64 warp instruction costs the same however few of its lanes are active,
+// so: a warp whose lanes all hold zero skips its butterfly (its sum is that
+// zero), maxima are of non-negative doubles, whose bit patterns order as
+// signed 64-bit integers (integer compares), and counts held in doubles are
+// added as 64-bit integers (exact, so in any order).
+__device__ __forceinline__ double warp_sum_nz(double v) {
+  if (!__any_sync(kFull, v != 0.0)) return v;
+  return warp_sum(v);
+}
+__device__ __forceinline__ long long warp_max_bits(long long b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long c = __shfl_xor_sync(kFull, b, o);
+    b = c > b ? c : b;
+  }
+  return b;
+}
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+  return __longlong_as_double(warp_max_bits(__double_as_longlong(v)));
+}
+__device__ __forceinline__ long long warp_isum(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+// red: at least 9 doubles of shared memory; every thread returns the result
 __device__ __forceinline__ double block_sum256(double v, double* red) {
-  red[threadIdx.x] = v;
+  v = warp_sum_nz(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = red[0];
 #pragma unroll
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+    for (int w = 1; w < 8; ++w) r += red[w];
+    red[8] = r;
   }
-  const double r = red[0];
   __syncthreads();
-  return r;
+  // red[8] is rewritten only after the next call's first barrier, which
+  // every thread reaches after this read
+  return red[8];
 }
+// v >= 0
 __device__ __forceinline__ double block_max256(double v, double* red) {
-  red[threadIdx.x] = v;
+  long long* rb = reinterpret_cast<long long*>(red);
+  const long long b = warp_max_bits(__double_as_longlong(v));
+  if ((threadIdx.x & 31) == 0) rb[threadIdx.x >> 5] = b;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    long long r = rb[0];
 #pragma unroll
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
+    for (int w = 1; w < 8; ++w) r = rb[w] > r ? rb[w] : r;
+    rb[8] = r;
   }
-  const double r = red[0];
   __syncthreads();
-  return r;
+  return __longlong_as_double(rb[8]);
 }
-// Sum of n doubles in a fixed order (strided per thread, then the tree).
+// integers held in doubles (|v| < 2^53), added exactly
+__device__ __forceinline__ double block_count256(long long v, double* red) {
+  long long* rb = reinterpret_cast<long long*>(red);
+  v = warp_isum(v);
+  if ((threadIdx.x & 31) == 0) rb[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long r = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) r += rb[w];
+    rb[8] = r;
+  }
+  __syncthreads();
+  return (double)rb[8];
+}
+// Sum of n doubles in a fixed order (strided per thread, then block_sum256).
 __device__ __forceinline__ double block_sum_array(const double* p, int n, double* red) {
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += 256) v += p[i];
   return block_sum256(v, red);
 }
+// p[i] >= 0
 __device__ __forceinline__ double block_max_array(const double* p, int n, double* red) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) v = fmax(v, p[i]);
-  return block_max256(v, red);
+  long long v = 0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const long long b = __double_as_longlong(p[i]);
+    v = b > v ? b : v;
+  }
+  return block_max256(__longlong_as_double(v), red);
+}
+__device__ __forceinline__ double block_count_array(const double* p, int n, double* red) {
+  long long v = 0;
+  for (int i = threadIdx.x; i < n; i += 256) v += (long long)p[i];
+  return block_count256(v, red);
 }
 
 // ------------------------------------------------------------------ K3b
@@ -885,7 +943,7 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
     __syncthreads();
     if (sh_last) {
       __threadfence();
-      const double nviol = block_sum_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
+      const double nviol = block_count_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
       const double mxv = block_max_array(a.k2part + 2 * a.k2_blocks, a.k2_blocks, red);
       if (threadIdx.x == 0) {
         DevState* st = a.st;
@@ -919,7 +977,8 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
   const int64_t j0 = lo + (int64_t)blockIdx.x * per;
   const int64_t j1 = min(hi, j0 + per);
   const double coef = a.use_coef ? a.st->coef : 0.0;
-  double psum = 0.0, nv = 0.0, mx = 0.0, preach = 0.0;
+  double psum = 0.0, mx = 0.0, preach = 0.0;
+  long long nv = 0;
   for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const int64_t i = a.rows ? a.rows[j] : j;
     const uint32_t m = a.mask[i];
@@ -957,9 +1016,9 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
           else if (fam == 1) gL += t.c * tt;
           else { gD -= c.bound * tt; gL += tt; }
           psum += c.prio;
-          nv += 1.0;
+          nv += 1;
           const double vu = (fam == 2) ? (xd > 0.0 ? viol / xd : 0.0) : viol;  // LETd in keV/um
-          mx = fmax(mx, vu);
+          mx = vu > mx ? vu : mx;
         }
       }
       const double sd = a.sD ? (double)a.sD[i] : 1.0;
@@ -968,29 +1027,48 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
     }
     a.gam[i] = out;
   }
-  // the block's three sums and its maximum in one fixed tree (each in the
-  // order of block_sum256 / block_max256)
-  __shared__ double red4[4][kRowThreads];
-  red4[0][threadIdx.x] = psum;
-  red4[1][threadIdx.x] = nv;
-  red4[2][threadIdx.x] = mx;
-  red4[3][threadIdx.x] = preach;
-  __syncthreads();
-#pragma unroll
-  for (int o = kRowThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red4[0][threadIdx.x] += red4[0][threadIdx.x + o];
-      red4[1][threadIdx.x] += red4[1][threadIdx.x + o];
-      red4[2][threadIdx.x] = fmax(red4[2][threadIdx.x], red4[2][threadIdx.x + o]);
-      red4[3][threadIdx.x] += red4[3][threadIdx.x + o];
-    }
-    __syncthreads();
+  // the block's two sums, its violated-row count and its largest violation
+  // (>= 0): warp reductions (the FP64 butterflies skipped by warps without
+  // violated or reachable rows), then the warp results in warp order
+  __shared__ double wred[3][kRowThreads / 32];
+  __shared__ long long wcnt[kRowThreads / 32];
+  psum = warp_sum_nz(psum);
+  preach = warp_sum_nz(preach);
+  nv = warp_isum(nv);
+  mx = warp_max_nonneg(mx);
+  if ((threadIdx.x & 31) == 0) {
+    const int wi = threadIdx.x >> 5;
+    wred[0][wi] = psum;
+    wred[1][wi] = preach;
+    wred[2][wi] = mx;
+    wcnt[wi] = nv;
   }
-  if (threadIdx.x == 0) {
-    a.part[blockIdx.x] = red4[0][0];
-    a.part[gridDim.x + blockIdx.x] = red4[1][0];
-    a.part[2 * gridDim.x + blockIdx.x] = red4[2][0];
-    a.part[3 * gridDim.x + blockIdx.x] = red4[3][0];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int k = threadIdx.x;
+    double t;
+    if (k == 1) {
+      long long c = 0;
+#pragma unroll
+      for (int w = 0; w < kRowThreads / 32; ++w) c += wcnt[w];
+      t = (double)c;
+    } else if (k == 2) {
+      long long b = 0;
+#pragma unroll
+      for (int w = 0; w < kRowThreads / 32; ++w) {
+        const long long x = __double_as_longlong(wred[2][w]);
+        b = x > b ? x : b;
+      }
+      t = __longlong_as_double(b);
+    } else {
+      const int src = k == 0 ? 0 : 1;
+      t = wred[src][0];
+#pragma unroll
+      for (int w = 1; w < kRowThreads / 32; ++w) t += wred[src][w];
+    }
+    // partial slices: sum of priorities of violated rows, violated rows,
+    // largest violation, sum of priorities of reachable rows
+    a.part[k * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -998,46 +1076,48 @@ __global__ void __launch_bounds__(kRowThreads) k_constraints(ConArgs a, Tables t
 
 // The partial sums (one per forward tile: tens of thousands) are added in
 // two fixed levels: every CTA sums one slice of each array, and the last CTA
-// to finish adds the slice sums in order and runs the trial loop.  FP64
-// additions are slow on a GB300 SM, so one CTA alone would take tens of us.
+// to finish adds the slice sums in order and runs the trial loop.  GB300's
+// FP64 rate is low and an FP64 warp instruction costs the same with one
+// active lane or 32, so each sum is laid out to need few of them: within a
+// CTA, warps 2k and 2k + 1 add array k (lane l of warp 2k + h takes the
+// elements 64 t + 32 h + l of the slice), each warp's lanes by a butterfly,
+// the two warps' results in warp order; the last CTA adds the 64 slice sums
+// of array k in warp k.  The solve state and the first trial steps are
+// loaded at the start, so that the last CTA's chain of dependent loads is
+// short.
 __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, int nf,
                                                 const double* part_bc, int nbc, const double* part_g,
-                                                int ng, DevState* st, double* stage) {
-  __shared__ double red[256];
-  __shared__ double red4[4][256];
-  __shared__ double sh_beta;
+                                                int ng, DevState* st, double* stage, const double* btab,
+                                                long long n_btab) {
+  __shared__ double wred[4][2];
+  __shared__ double tot_sh[4];
   __shared__ bool sh_last;
   const int G = gridDim.x, b = blockIdx.x;
-  // the four sums of this block's slices at once: per thread a strided sum,
-  // then one fixed tree for all four (the order of each sum is that of
-  // block_sum_array)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // state read by the last CTA (written only by it, at its end, in this kernel)
+  const long long s0 = st->s;
+  const int max_trials = st->max_trials;
+  const int grad_normalize = st->grad_normalize;
+  const double f_empty = st->f_empty;
+  double beta_pre = 0.0;  // step of trial `lane` (first round)
+  if (wid == 0 && lane < max_trials) {
+    const long long si = s0 + lane;
+    if (si < n_btab) beta_pre = btab[si];
+  }
   {
-    const double* arr[4] = {part_f, part_bc, part_bc + nbc, part_g};
-    const int len[4] = {nf, nbc, nbc, ng};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int per = (len[k] + G - 1) / G;
-      const int i0 = min(len[k], b * per), i1 = min(len[k], i0 + per);
-      double v = 0.0;
-      for (int i = i0 + threadIdx.x; i < i1; i += 256) v += arr[k][i];
-      red4[k][threadIdx.x] = v;
-    }
+    const int k = wid >> 1, h = wid & 1;
+    const double* arr = k == 0 ? part_f : k == 1 ? part_bc : k == 2 ? part_bc + nbc : part_g;
+    const int len = k == 0 ? nf : k == 3 ? ng : nbc;
+    const int per = (len + G - 1) / G;
+    const int i0 = min(len, b * per), i1 = min(len, i0 + per);
+    double v = 0.0;
+    for (int i = i0 + 32 * h + lane; i < i1; i += 64) v += arr[i];
+    v = warp_sum_nz(v);
+    if (lane == 0) wred[k][h] = v;
   }
   __syncthreads();
-#pragma unroll
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) red4[k][threadIdx.x] += red4[k][threadIdx.x + o];
-    }
-    __syncthreads();
-  }
+  if (threadIdx.x < 4) stage[threadIdx.x * G + b] = wred[threadIdx.x][0] + wred[threadIdx.x][1];
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) stage[k * G + b] = red4[k][0];
-    // the step of trial b of this iteration, ready for the last block (the
-    // pow, slow in FP64, overlaps the other blocks' sums)
-    stage[4 * G + b] = st->beta0 * pow(st->alpha, (double)(st->s + b));
     __threadfence();
     sh_last = atomicAdd(&st->done_fin, 1u) == (unsigned)G - 1;
   }
@@ -1045,64 +1125,55 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   if (!sh_last) return;
   __threadfence();
   // the slice sums, written by other CTAs of this launch: read past L1
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  if (wid < 4) {
     double v = 0.0;
-    for (int i = threadIdx.x; i < G; i += 256) v += __ldcg(&stage[k * G + i]);
-    red4[k][threadIdx.x] = v;
+    for (int i = lane; i < G; i += 32) v += __ldcg(&stage[wid * G + i]);
+    v = warp_sum_nz(v);
+    if (lane == 0) tot_sh[wid] = v;
   }
   __syncthreads();
-#pragma unroll
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) red4[k][threadIdx.x] += red4[k][threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  const double f = red4[0][0] + (step == 0 ? st->f_empty : 0.0);
-  const double Bp = red4[1][0];
-  const double Cp = red4[2][0];
-  const double gn2 = red4[3][0];
+  if (wid != 0) return;
+  const double f = tot_sh[0] + (step == 0 ? f_empty : 0.0);
+  const double Bp = tot_sh[1];
+  const double Cp = tot_sh[2];
+  const double gn2 = tot_sh[3];
   // The trial loop of Fig. 3 (beta = beta0 alpha^s, s advancing on every
   // trial, accept the first trial that does not ascend, at most max_trials):
-  // the block evaluates consecutive trials at once, each thread one, and
-  // takes the first accepted one (a block minimum of the trial index), so
-  // the decision and s are those of the trials taken in turn.  The steps of
-  // the first 64 trials were computed by the 64 blocks; later rounds of 256
-  // trials compute their own (an FP64 pow each, slow on GB300).
-  const long long s0 = st->s;
-  const int max_trials = st->max_trials;
+  // the warp evaluates 32 consecutive trials at once, one per lane, and takes
+  // the lowest accepting lane, so the decision and s are those of the trials
+  // taken in turn.  The steps beta0 alpha^s come from the table the host
+  // filled at fredopt_begin (s < n_btab), else from an FP64 pow.
   const double gn = gn2 > 0.0 ? sqrt(gn2) : 0.0;
   double B = 0.0, C = 0.0;
   if (gn2 > 0.0) {
-    if (st->grad_normalize) { B = -Bp / gn; C = Cp / gn2; }
+    if (grad_normalize) { B = -Bp / gn; C = Cp / gn2; }
     else { B = -Bp; C = Cp; }
   }
   int first = max_trials;  // index of the accepted trial, max_trials if none
+  double beta_acc = 0.0;
   if (gn2 > 0.0) {
-    for (int base = 0, width = 64; base < max_trials && first == max_trials; base += width, width = 256) {
-      const int tr = base + (int)threadIdx.x;
-      double cand = (double)max_trials;
+    for (int base = 0; base < max_trials; base += 32) {
+      const int tr = base + lane;
       double beta = 0.0;
-      if ((int)threadIdx.x < width && tr < max_trials) {
-        beta = tr < G ? __ldcg(&stage[4 * G + tr]) : st->beta0 * pow(st->alpha, (double)(s0 + tr));
+      bool ok = false;
+      if (tr < max_trials) {
+        const long long si = s0 + tr;
+        beta = base == 0 && si < n_btab ? beta_pre
+             : si < n_btab              ? btab[si]
+                                        : st->beta0 * pow(st->alpha, (double)si);
         const double df = beta * (2.0 * B + beta * C);  // f(x + beta v) - f(x), Eq. 2 is quadratic
-        if (df <= 0.0) cand = (double)tr;
+        ok = df <= 0.0;
       }
-      red[threadIdx.x] = cand;
-      __syncthreads();
-#pragma unroll
-      for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
+      const unsigned acc = __ballot_sync(kFull, ok);
+      if (acc) {
+        const int l = __ffs(acc) - 1;
+        first = base + l;
+        beta_acc = __shfl_sync(kFull, beta, l);
+        break;
       }
-      first = (int)red[0];
-      if (tr == first) sh_beta = beta;  // the accepted trial's step
-      __syncthreads();
     }
   }
-  if (threadIdx.x != 0) return;
+  if (lane != 0) return;
   st->done_fin = 0u;
   if (step == 0) {
     st->f_start = f;
@@ -1115,8 +1186,8 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   if (gn2 > 0.0) {
     st->gnorm = gn;
     if (first < max_trials) {
-      const double beta = sh_beta;
-      coef = st->grad_normalize ? -beta / gn : -beta;
+      const double beta = beta_acc;
+      coef = grad_normalize ? -beta / gn : -beta;
       st->accepted += 1;
       st->accepted_total += 1;
       st->beta_acc = beta;
@@ -1658,8 +1729,9 @@ void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cu
 }
 
 void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
-                   const double* part_g, int ng, DevState* st, double* stage, cudaStream_t s) {
-  k_finish<<<kFinishBlocks, 256, 0, s>>>(step, part_f, nf, part_bc, nbc, part_g, ng, st, stage);
+                   const double* part_g, int ng, DevState* st, double* stage, const double* btab,
+                   long long n_btab, cudaStream_t s) {
+  k_finish<<<kFinishBlocks, 256, 0, s>>>(step, part_f, nf, part_bc, nbc, part_g, ng, st, stage, btab, n_btab);
 }
 
 void launch_apply_step(int64_t n_hot, int n, float* w, const float* g, float2* yw, const float2* yg,
@@ -1939,7 +2011,7 @@ __global__ void __launch_bounds__(256) k_sweep_update(SweepArgs a) {
   __shared__ double sh_scale;
   const double W = block_sum_array(a.k2part + (a.norm == 1 ? 0 : 3 * a.k2_blocks), a.k2_blocks, red);
   if (a.in_solve && blockIdx.x == 0) {
-    const double nv = block_sum_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
+    const double nv = block_count_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
     const double mx = block_max_array(a.k2part + 2 * a.k2_blocks, a.k2_blocks, red);
     if (threadIdx.x == 0) {
       a.st->sweep_nv += nv;
