@@ -621,6 +621,10 @@ void enqueue_iteration(fredopt_t h) {
   cc.norm = h->prm.cimmino_norm;
   cc.lam = h->lam;
   cc.in_solve = 1;
+  // norm ALL without decay: the scale lam eta^k / W_all is fixed (the same
+  // FP64 operations the kernel would do)
+  cc.has_scale = (cc.norm != FREDOPT_NORM_VIOLATED && h->prm.eta == 1.0) ? 1 : 0;
+  cc.scale = h->W_all > 0.0 ? cc.lam * 1.0 / h->W_all : 0.0;
   run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
 }
 
@@ -1707,6 +1711,8 @@ int fredopt_feasibility_step(fredopt_t h, const float* x, double relaxation, dou
   cc.lam = relaxation;
   cc.prio_scale = prio_scale;
   cc.in_solve = 0;
+  cc.has_scale = norm != FREDOPT_NORM_VIOLATED ? 1 : 0;
+  cc.scale = h->W_all > 0.0 ? relaxation * prio_scale / h->W_all : 0.0;
   run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
   CK(cudaGetLastError());
   CK(copy_out(h, w_out, h->xbuf.p, (size_t)h->n * sizeof(float), flags));

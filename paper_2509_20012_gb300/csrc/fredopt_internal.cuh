@@ -144,6 +144,8 @@ struct ColArgs {
   double lam;
   double W_all;
   int32_t in_solve;          // COL_PROJ: 1 = scale from DevState (eta^k) and advance k
+  int32_t has_scale;         // COL_PROJ: 1 = the scale lam ps / W is `scale` (norm ALL, eta^k = 1)
+  double scale;
   int32_t use_u;             // 0: no transposed product (no constraints): u = 0
   DevState* st;
   LogEntry* log;

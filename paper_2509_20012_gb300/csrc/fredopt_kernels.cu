@@ -894,7 +894,8 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
   __shared__ double red[kColThreads];
   __shared__ double sh_scale;
   __shared__ bool sh_last;
-  if (MODE == COL_PROJ) {
+  double scale = a.scale;  // COL_PROJ with has_scale: lam ps / W from the host
+  if (MODE == COL_PROJ && !a.has_scale) {
     double W = a.W_all;
     if (a.norm == 1) W = block_sum_array(a.k2part, a.k2_blocks, red);
     if (threadIdx.x == 0) {
@@ -902,6 +903,7 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
       sh_scale = W > 0.0 ? a.lam * ps / W : 0.0;
     }
     __syncthreads();
+    scale = sh_scale;
   }
   const double coef = (MODE == COL_PROJ && a.use_coef) ? a.st->coef : 0.0;
   const int per = (a.n + gridDim.x - 1) / gridDim.x;
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
     } else {
       double xj = (double)a.w[j];
       if (a.use_coef) xj += coef * (double)a.g[j];
-      const double wn = xj + sh_scale * (double)s;
+      const double wn = xj + scale * (double)s;
       a.w[j] = wn > 0.0 ? (float)wn : 0.0f;
     }
   }
@@ -1144,9 +1146,10 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   // taken in turn.  The steps beta0 alpha^s come from the table the host
   // filled at fredopt_begin (s < n_btab), else from an FP64 pow.
   const double gn = gn2 > 0.0 ? sqrt(gn2) : 0.0;
+  const double ig = gn2 > 0.0 ? 1.0 / gn : 0.0;  // one FP64 division for B, C and the step
   double B = 0.0, C = 0.0;
   if (gn2 > 0.0) {
-    if (grad_normalize) { B = -Bp / gn; C = Cp / gn2; }
+    if (grad_normalize) { B = -Bp * ig; C = Cp * ig * ig; }
     else { B = -Bp; C = Cp; }
   }
   int first = max_trials;  // index of the accepted trial, max_trials if none
@@ -1187,7 +1190,7 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
     st->gnorm = gn;
     if (first < max_trials) {
       const double beta = beta_acc;
-      coef = grad_normalize ? -beta / gn : -beta;
+      coef = grad_normalize ? -beta * ig : -beta;
       st->accepted += 1;
       st->accepted_total += 1;
       st->beta_acc = beta;
