@@ -625,6 +625,7 @@ void enqueue_iteration(fredopt_t h) {
   // FP64 operations the kernel would do)
   cc.has_scale = (cc.norm != FREDOPT_NORM_VIOLATED && h->prm.eta == 1.0) ? 1 : 0;
   cc.scale = h->W_all > 0.0 ? cc.lam * 1.0 / h->W_all : 0.0;
+  cc.log_block = cc.has_scale;
   run(h, 3, [&] { launch_colfinish(G, COL_PROJ, cc, s); });
 }
 

@@ -146,6 +146,8 @@ struct ColArgs {
   int32_t in_solve;          // COL_PROJ: 1 = scale from DevState (eta^k) and advance k
   int32_t has_scale;         // COL_PROJ: 1 = the scale lam ps / W is `scale` (norm ALL, eta^k = 1)
   double scale;
+  int32_t log_block;         // COL_PROJ in a solve with has_scale: 1 = one extra block closes the
+                             // iteration (no block reads k), instead of the last block to finish
   int32_t use_u;             // 0: no transposed product (no constraints): u = 0
   DevState* st;
   LogEntry* log;

@@ -889,11 +889,44 @@ __device__ __forceinline__ double block_count_array(const double* p, int n, doub
 
 // ------------------------------------------------------------------ K3b
 
+// The end of an iteration (block-wide): its log entry (violated rows and
+// largest violation from the constraint partials, the solve state written by
+// the scalar finish) and k <- k + 1.
+__device__ __forceinline__ void close_iteration(const ColArgs& a, double* red) {
+  const double nviol = block_count_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
+  const double mxv = block_max_array(a.k2part + 2 * a.k2_blocks, a.k2_blocks, red);
+  if (threadIdx.x == 0) {
+    DevState* st = a.st;
+    if (st->log_cap > 0) {
+      LogEntry e;
+      e.k = st->k;
+      e.s = st->s;
+      e.accepted = st->accepted;
+      e.n_violated = (int)nviol;
+      e.beta = st->beta_acc;
+      e.f_start = st->f_start;
+      e.f_end = st->f_cur;
+      e.gnorm = st->gnorm;
+      e.max_violation = mxv;
+      a.log[st->k % st->log_cap] = e;
+    }
+    st->k += 1;
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
   __shared__ double red[kColThreads];
   __shared__ double sh_scale;
   __shared__ bool sh_last;
+  // COL_PROJ with log_block: the launch's last block closes the iteration,
+  // concurrently with the others (nothing else in the launch reads k), and
+  // the other blocks split the columns
+  const int nb = (int)gridDim.x - (MODE == COL_PROJ ? a.log_block : 0);
+  if (MODE == COL_PROJ && a.log_block && (int)blockIdx.x == nb) {
+    close_iteration(a, red);
+    return;
+  }
   double scale = a.scale;  // COL_PROJ with has_scale: lam ps / W from the host
   if (MODE == COL_PROJ && !a.has_scale) {
     double W = a.W_all;
@@ -906,7 +939,7 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
     scale = sh_scale;
   }
   const double coef = (MODE == COL_PROJ && a.use_coef) ? a.st->coef : 0.0;
-  const int per = (a.n + gridDim.x - 1) / gridDim.x;
+  const int per = (a.n + nb - 1) / nb;
   const int j0 = blockIdx.x * per, j1 = min(a.n, j0 + per);
   double acc = 0.0;
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
@@ -934,7 +967,7 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
     acc = block_sum256(acc, red);
     if (threadIdx.x == 0) a.part[blockIdx.x] = acc;
   }
-  if (MODE == COL_PROJ && a.in_solve) {
+  if (MODE == COL_PROJ && a.in_solve && !a.log_block) {
     // the last block to finish closes the iteration: log entry, k <- k + 1
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -945,26 +978,8 @@ __global__ void __launch_bounds__(kColThreads) k_colfinish(ColArgs a) {
     __syncthreads();
     if (sh_last) {
       __threadfence();
-      const double nviol = block_count_array(a.k2part + a.k2_blocks, a.k2_blocks, red);
-      const double mxv = block_max_array(a.k2part + 2 * a.k2_blocks, a.k2_blocks, red);
-      if (threadIdx.x == 0) {
-        DevState* st = a.st;
-        if (st->log_cap > 0) {
-          LogEntry e;
-          e.k = st->k;
-          e.s = st->s;
-          e.accepted = st->accepted;
-          e.n_violated = (int)nviol;
-          e.beta = st->beta_acc;
-          e.f_start = st->f_start;
-          e.f_end = st->f_cur;
-          e.gnorm = st->gnorm;
-          e.max_violation = mxv;
-          a.log[st->k % st->log_cap] = e;
-        }
-        st->k += 1;
-        st->done = 0u;
-      }
+      close_iteration(a, red);
+      if (threadIdx.x == 0) a.st->done = 0u;
     }
   }
 }
@@ -1724,7 +1739,7 @@ void launch_backward(const Geometry& g, int fmt, bool stream_hint, bool use_D, c
 void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_t s) {
   if (mode == COL_OUT) k_colfinish<COL_OUT><<<g.col_blocks, kColThreads, 0, s>>>(a);
   else if (mode == COL_GRAD) k_colfinish<COL_GRAD><<<g.col_blocks, kColThreads, 0, s>>>(a);
-  else k_colfinish<COL_PROJ><<<g.col_blocks, kColThreads, 0, s>>>(a);
+  else k_colfinish<COL_PROJ><<<g.col_blocks + a.log_block, kColThreads, 0, s>>>(a);
 }
 
 void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s, int grid) {
