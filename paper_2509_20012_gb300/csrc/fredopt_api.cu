@@ -138,14 +138,14 @@ struct fredopt_ctx {
   DBuf<float> xs;                            // the point being swept [n_pad]
   DBuf<float2> ys;                           // forward product of the block rows [n_hot]
   DBuf<double> part;
-  // steps beta0 alpha^s of the trial loop for s < kBetaTable, computed on
-  // the host for the (alpha, beta0) of the last fredopt_begin
-  DBuf<double> btab;
+  // steps beta0 alpha^s of the trial loop for s < kBetaTable (in `part` at
+  // off_btab), filled on the device for (btab_alpha, btab_beta0)
   double btab_alpha = -1.0, btab_beta0 = -1.0;
   DBuf<DevState> st;
   DBuf<LogEntry> log;
   DBuf<int> errw;
-  size_t off_f = 0, off_bc = 0, off_g = 0, off_k2 = 0, off_fin = 0, off_cnt = 0, off_stage = 0, n_part = 0;
+  size_t off_f = 0, off_bc = 0, off_g = 0, off_k2 = 0, off_fin = 0, off_cnt = 0, off_stage = 0, off_btab = 0,
+         n_part = 0;
 
   // solve
   bool begun = false;
@@ -595,7 +595,7 @@ void enqueue_iteration(fredopt_t h) {
       run(h, 0, [&] { launch_forward(G, h->fmt, EPI_BC, h->hint_fwd, fb, t, s); });
       run(h, 4, [&] {
         launch_finish(step, part_f, nf, part_bc, fa.n_warps, part_g, G.col_blocks, h->st.p,
-                      h->part.p + h->off_stage, h->btab.p, kBetaTable, s);
+                      h->part.p + h->off_stage, h->part.p + h->off_btab, kBetaTable, s);
       });
     }
   } else {
@@ -1225,7 +1225,9 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   h->off_fin = h->off_k2 + 4 * G.row_blocks;
   h->off_cnt = h->off_fin + 8 * G.row_blocks;
   h->off_stage = h->off_cnt + 3 * G.row_blocks;
-  h->n_part = h->off_stage + 4 * kFinishBlocks;
+  h->off_btab = h->off_stage + 4 * kFinishBlocks;
+  h->n_part = h->off_btab + kBetaTable;
+  h->btab_alpha = -1.0;  // the table is refilled at the next fredopt_begin
   CK(h->part.alloc(h->n_part));
   CK(cudaMemsetAsync(h->part.p, 0, h->n_part * sizeof(double), s));
   h->y64.release(); h->yall.release(); h->fout_a.release(); h->fout_b.release();
@@ -1350,11 +1352,10 @@ int fredopt_begin(fredopt_t h, const float* w0, double alpha, double relaxation,
   h->beta0 = p.beta0 < 0.0 ? 0.1 * std::sqrt(nrm) : p.beta0;
   h->tab.c = p.c_cdl;
   CK(cudaMemcpyAsync(h->w.p, hw.data(), h->n * sizeof(float), cudaMemcpyHostToDevice, s));
-  if (h->btab_alpha != alpha || h->btab_beta0 != h->beta0 || !h->btab.p) {
-    std::vector<double> bt(kBetaTable);
-    for (int64_t i = 0; i < kBetaTable; ++i) bt[i] = h->beta0 * std::pow(alpha, (double)i);
-    CK(upload_vec(h, h->btab, bt));
-    CK(cudaStreamSynchronize(s));  // bt is pageable and goes out of scope
+  if (h->btab_alpha != alpha || h->btab_beta0 != h->beta0) {
+    // asynchronous: no allocation or host synchronisation in a served begin
+    launch_beta_table(h->part.p + h->off_btab, kBetaTable, h->beta0, alpha, s);
+    CK(cudaGetLastError());
     h->btab_alpha = alpha;
     h->btab_beta0 = h->beta0;
   }

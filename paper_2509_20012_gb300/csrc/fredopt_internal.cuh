@@ -206,8 +206,9 @@ void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_
 // grid 0: g.row_blocks CTAs (the partials' stride); otherwise that many
 void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s, int grid = 0);
 constexpr int kFinishBlocks = 64;  // CTAs of the scalar finish; stage holds 4 * kFinishBlocks doubles
-// btab[s] = beta0 alpha^s for s < n_btab (host-computed at fredopt_begin)
+// btab[s] = beta0 alpha^s for s < n_btab (filled at fredopt_begin)
 constexpr long long kBetaTable = 1 << 16;
+void launch_beta_table(double* out, long long n, double beta0, double alpha, cudaStream_t s);
 void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
                    const double* part_g, int ng, DevState* st, double* stage, const double* btab,
                    long long n_btab, cudaStream_t s);

@@ -1158,8 +1158,8 @@ __global__ void __launch_bounds__(256) k_finish(int step, const double* part_f, 
   // trial, accept the first trial that does not ascend, at most max_trials):
   // the warp evaluates 32 consecutive trials at once, one per lane, and takes
   // the lowest accepting lane, so the decision and s are those of the trials
-  // taken in turn.  The steps beta0 alpha^s come from the table the host
-  // filled at fredopt_begin (s < n_btab), else from an FP64 pow.
+  // taken in turn.  The steps beta0 alpha^s come from the table filled at
+  // fredopt_begin (s < n_btab), else from the same FP64 expression.
   const double gn = gn2 > 0.0 ? sqrt(gn2) : 0.0;
   const double ig = gn2 > 0.0 ? 1.0 / gn : 0.0;  // one FP64 division for B, C and the step
   double B = 0.0, C = 0.0;
@@ -1744,6 +1744,15 @@ void launch_colfinish(const Geometry& g, int mode, const ColArgs& a, cudaStream_
 
 void launch_constraints(const Geometry& g, const Tables& t, const ConArgs& a, cudaStream_t s, int grid) {
   k_constraints<<<grid > 0 ? grid : g.row_blocks, kRowThreads, 0, s>>>(a, t);
+}
+
+__global__ void k_beta_table(double* out, long long n, double beta0, double alpha) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = beta0 * pow(alpha, (double)i);
+}
+
+void launch_beta_table(double* out, long long n, double beta0, double alpha, cudaStream_t s) {
+  if (n > 0) k_beta_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, beta0, alpha);
 }
 
 void launch_finish(int step, const double* part_f, int nf, const double* part_bc, int nbc,
