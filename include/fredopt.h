@@ -498,8 +498,9 @@ typedef struct fredopt_ticket_info {
 typedef struct fredopt_server* fredopt_server_t;
 
 /* Estimate of the device memory one plan needs while it loads and runs: the
- * peak of the load and the resident CSR, CSC, based row offsets with their
- * block headers, vectors and tables.  The overflow table of wide 128-element
+ * peak of the load (including the CSC build's scratch of one record per
+ * nonzero: 16 bytes with FP32 values, 8 with 16-bit) and the resident CSR,
+ * CSC, based row offsets with their block headers, vectors and tables.  The overflow table of wide 128-element
  * blocks (rows spanning 65536 or more) is counted for one such block per
  * column boundary plus one in 16 blocks; for plans with sparser rows the
  * estimate can be low, and a load that then does not fit fails with

@@ -1017,11 +1017,10 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(cudaMemsetAsync(D_d.p + nnz, 0, (nnz_alloc - nnz) * sizeof(float), s));
     CK(cudaMemsetAsync(L_d.p + nnz, 0, (nnz_alloc - nnz) * sizeof(float), s));
     if (perm) {
-      DBuf<int64_t> src_row;
-      CK(upload_vec(h, src_row, order));
-      launch_gather_rows(rp_in.p, src_row.p, h->rp.p, n_vox, colp, Dp, Lp, col_d.p, D_d.p, L_d.p, s);
-      CK(cudaGetLastError());
+      // device row -> voxel: the gather's source rows, kept for the outputs
       CK(upload_vec(h, h->voxel, order));
+      launch_gather_rows(rp_in.p, h->voxel.p, h->rp.p, n_vox, colp, Dp, Lp, col_d.p, D_d.p, L_d.p, s);
+      CK(cudaGetLastError());
       CK(cudaStreamSynchronize(s));
     } else if (nnz) {
       CK(cudaMemcpyAsync(col_d.p, col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
@@ -1059,9 +1058,10 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   h->V = n_vox; h->nnz = nnz; h->n = n_spots; h->n_pad = (n_spots + 3) & ~3;
   h->fmt = fmt; h->roi = roi; h->perm = perm; h->n_hot = n_hot; h->nnz_hot = rpd[n_hot];
   h->n_hot_ne = n_hot_ne; h->n_cold_ne = n_cold_ne;
-  h->h_voxel = perm ? std::vector<int64_t>(order.begin(), order.end()) : std::vector<int64_t>();
   h->h_mask.resize(n_hot);
   for (int64_t r = 0; r < n_hot; ++r) h->h_mask[r] = m0[order[r]];
+  if (perm) h->h_voxel = std::move(order);  // order is not used below
+  else h->h_voxel.clear();
   CK(upload_vec(h, h->mask, h->h_mask));
   {
     // the constraint evaluation visits only these rows; the others' projection
@@ -1112,9 +1112,17 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
     CK(cudaMemsetAsync(h->DTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
     CK(cudaMemsetAsync(h->LTv.p + (size_t)h->nnz_hot * vb, 0, (size_t)(nh_alloc - h->nnz_hot) * vb, s));
     CK(cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
-    if (n_hot_ne > 0)
+    if (n_hot_ne > 0) {
+      // scattered stores are limited by their count: one record per entry,
+      // split into the three arrays by a coalesced pass (scratch freed here)
+      DBuf<uint8_t> rec;
+      const size_t rb = csc_fill_rec_bytes(h->geo, fmt, n_spots);
+      if (rb) CK(rec.alloc((size_t)h->nnz_hot * rb));
       launch_csc_fill(h->geo, fmt, h->rp.p, h->col.p, h->Dv.p, h->Lv.p, blk_d.p, n_blk, n_spots, cnt.p,
-                      h->crow.p, h->DTv.p, h->LTv.p, h->errw.p, s);
+                      h->crow.p, h->DTv.p, h->LTv.p, h->errw.p, rb ? rec.p : nullptr, h->nnz_hot, s);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(s));
+    }
     CK(cudaGetLastError());
     int ferr = 0;
     CK(cudaMemcpyAsync(&ferr, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, s));

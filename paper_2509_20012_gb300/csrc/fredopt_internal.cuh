@@ -244,9 +244,13 @@ void launch_csc_count(const int64_t* rp, const int32_t* col, const int64_t* blk_
                       int32_t n_cols, int32_t* cnt, cudaStream_t s);
 void launch_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int64_t* cp, cudaStream_t s);
 // stable CSR -> CSC scatter; a bulk-copy wait that gives up sets bit 0 of *err
+// rec: null, or csc_fill_rec_bytes(...) bytes per output entry of scratch
+// (n_out entries): the fill then stores one record per entry and splits them
 void launch_csc_fill(const Geometry& g, int fmt, const int64_t* rp, const int32_t* col, const void* Dv,
                      const void* Lv, const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor,
-                     int32_t* row_out, void* DT, void* LT, int* err, cudaStream_t s);
+                     int32_t* row_out, void* DT, void* LT, int* err, void* rec, int64_t n_out, cudaStream_t s);
+// bytes per entry of the fill's record scratch for this plan, 0 for none
+size_t csc_fill_rec_bytes(const Geometry& g, int fmt, int32_t n_cols);
 void launch_csc_colsum(const int32_t* cnt, int n_blk, int32_t n_cols, int64_t* tot, cudaStream_t s);
 void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_t* row, const void* DT,
                         const void* LT, const float* sD, const float* sL, float* Dout, float* Lout,

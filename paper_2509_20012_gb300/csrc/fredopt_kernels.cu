@@ -1864,14 +1864,206 @@ void launch_csc_offsets(int32_t* cnt, int n_blk, int32_t n_cols, const int64_t* 
   k_csc_offsets<<<(n_cols + 255) / 256, 256, 0, s>>>(cnt, n_blk, n_cols, cp);
 }
 
+// The same stable transpose, rows taken kFillWinRows at a time: the order of
+// a column's entries within a window of rows is recovered from a per-column
+// bit mask of the window rows that hold the column, so a window costs three
+// block barriers instead of one per row.  For each window:
+//   A  every entry (row r, column c) sets bit r - g0 of mask[c] (atomic OR,
+//      order-independent);
+//   B  it goes to position cur[c] + popc(mask[c] below bit r - g0): the rows
+//      of the window before r that hold c come first, as in row order;
+//   C  the first entry of each column advances cur[c] by popc(mask[c]) and
+//      clears the mask.
+// Two 16-bit masks share a 32-bit word.  Shared memory: the block's cursors
+// and masks (6 bytes per column) and a chunk of row pointers.  The result
+// equals k_csc_fill's bit for bit.
+constexpr int kFillWinRows = 16;
+constexpr int kFillK = 2;  // entries per thread a window holds in registers (else the loop form)
+#ifndef FO_FILL_WIN
+#define FO_FILL_WIN 1  // 0: the row-by-row k_csc_fill for every plan
+#endif
+#ifndef FO_FILL_REC
+#define FO_FILL_REC 1  // 1: the window fill stores records, then k_csc_split
+#endif
+
+__device__ __forceinline__ int fill_win_row(const int64_t* wrp, int nr, int64_t p) {
+  int lo = 0, hi = nr - 1;  // the window row r with wrp[r] <= p < wrp[r + 1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (wrp[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// With `rec`, an entry is one record store (row and both values: 16 bytes
+// for FP32, 8 for 16-bit values) instead of three scattered 4- or 2-byte
+// stores, and k_csc_split writes the three arrays afterwards with coalesced
+// stores: scattered stores are limited by their count, not their bytes.
+template <typename VT> struct FillRec;
+template <> struct FillRec<float> { using T = int4; };
+template <> struct FillRec<uint16_t> { using T = uint2; };
+__device__ __forceinline__ int4 fill_rec(int32_t r, float d, float l) {
+  return make_int4(r, __float_as_int(d), __float_as_int(l), 0);
+}
+__device__ __forceinline__ uint2 fill_rec(int32_t r, uint16_t d, uint16_t l) {
+  return make_uint2((uint32_t)r, (uint32_t)d | ((uint32_t)l << 16));
+}
+
+template <typename VT>
+__global__ void k_csc_split(const typename FillRec<VT>::T* __restrict__ rec, int64_t n, int32_t* __restrict__ row_out,
+                            VT* __restrict__ DT, VT* __restrict__ LT) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const auto v = rec[i];
+  if constexpr (sizeof(VT) == 4) {
+    row_out[i] = v.x;
+    DT[i] = __int_as_float(v.y);
+    LT[i] = __int_as_float(v.z);
+  } else {
+    row_out[i] = (int32_t)v.x;
+    DT[i] = (uint16_t)(v.y & 0xffffu);
+    LT[i] = (uint16_t)(v.y >> 16);
+  }
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kFillThreads) k_csc_fill_win(
+    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ Dv,
+    const VT* __restrict__ Lv, const int64_t* __restrict__ blk_row, int32_t n_cols,
+    const int32_t* __restrict__ cursor, int32_t* __restrict__ row_out, VT* __restrict__ DT,
+    VT* __restrict__ LT, typename FillRec<VT>::T* __restrict__ rec) {
+  extern __shared__ __align__(16) unsigned char fill_sh[];
+  int32_t* cur = reinterpret_cast<int32_t*>(fill_sh);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(fill_sh + (size_t)n_cols * sizeof(int32_t));
+  int64_t* srp = reinterpret_cast<int64_t*>(
+      fill_sh + (((size_t)n_cols * sizeof(int32_t) + (size_t)((n_cols + 1) / 2) * sizeof(uint32_t) + 15) & ~(size_t)15));
+  const int b = blockIdx.x;
+  const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
+  if (r0 >= r1) return;
+  const int32_t* gcur = cursor + (int64_t)b * n_cols;
+  for (int j = threadIdx.x; j < n_cols; j += blockDim.x) cur[j] = gcur[j];
+  for (int j = threadIdx.x; j < (n_cols + 1) / 2; j += blockDim.x) mask[j] = 0u;
+  // row pointers staged kFillRows rows at a time; windows of kFillWinRows rows
+  for (int64_t c0 = r0; c0 < r1; c0 += kFillRows) {
+    const int nc = (int)(r1 - c0 < kFillRows ? r1 - c0 : kFillRows);
+    __syncthreads();  // the previous chunk is done with srp, cur and mask
+    for (int i = threadIdx.x; i <= nc; i += blockDim.x) srp[i] = rp[c0 + i];
+    __syncthreads();
+    for (int w0 = 0; w0 < nc; w0 += kFillWinRows) {
+      const int nr = nc - w0 < kFillWinRows ? nc - w0 : kFillWinRows;
+      const int64_t* wrp = srp + w0;
+      const int64_t g0 = c0 + w0;
+      const int64_t e0 = wrp[0], e1 = wrp[nr];
+      if (w0 > 0) __syncthreads();  // the previous window's C is done with cur and mask
+      if (e1 - e0 <= (int64_t)kFillK * kFillThreads) {
+        // the window's entries in registers: one round of loads, then the
+        // three steps on shared memory only
+        int cc[kFillK], rr[kFillK];
+        VT dv[kFillK], lv[kFillK];
+#pragma unroll
+        for (int k = 0; k < kFillK; ++k) {
+          const int64_t p = e0 + threadIdx.x + (int64_t)k * kFillThreads;
+          cc[k] = -1;
+          if (p < e1) {
+            cc[k] = col[p];
+            dv[k] = Dv[p];
+            lv[k] = Lv[p];
+            rr[k] = fill_win_row(wrp, nr, p);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kFillK; ++k)
+          if (cc[k] >= 0) atomicOr(&mask[cc[k] >> 1], 1u << ((cc[k] & 1) * 16 + rr[k]));
+        __syncthreads();
+        uint32_t mk[kFillK];
+#pragma unroll
+        for (int k = 0; k < kFillK; ++k) {
+          if (cc[k] < 0) continue;
+          const int c = cc[k], r = rr[k];
+          mk[k] = (mask[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
+          const int32_t pos = cur[c] + __popc(mk[k] & ((1u << r) - 1u));
+          if (rec) {
+            rec[pos] = fill_rec((int32_t)(g0 + r), dv[k], lv[k]);
+          } else {
+            row_out[pos] = (int32_t)(g0 + r);
+            DT[pos] = dv[k];
+            LT[pos] = lv[k];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kFillK; ++k) {
+          if (cc[k] < 0) continue;
+          const int c = cc[k];
+          if ((mk[k] & ((1u << rr[k]) - 1u)) == 0u) {  // the column's first row in the window
+            cur[c] += __popc(mk[k]);
+            atomicAnd(&mask[c >> 1], ~(0xffffu << ((c & 1) * 16)));
+          }
+        }
+        continue;
+      }
+      // A: the window rows that hold each column
+      for (int64_t p = e0 + threadIdx.x; p < e1; p += kFillThreads) {
+        const int c = col[p];
+        const int r = fill_win_row(wrp, nr, p);
+        atomicOr(&mask[c >> 1], 1u << ((c & 1) * 16 + r));
+      }
+      __syncthreads();
+      // B: each entry to its place
+      for (int64_t p = e0 + threadIdx.x; p < e1; p += kFillThreads) {
+        const int c = col[p];
+        const int r = fill_win_row(wrp, nr, p);
+        const uint32_t m = (mask[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
+        const int32_t pos = cur[c] + __popc(m & ((1u << r) - 1u));
+        if (rec) {
+          rec[pos] = fill_rec((int32_t)(g0 + r), Dv[p], Lv[p]);
+        } else {
+          row_out[pos] = (int32_t)(g0 + r);
+          DT[pos] = Dv[p];
+          LT[pos] = Lv[p];
+        }
+      }
+      __syncthreads();
+      // C: advance the cursors past the window, clear the masks
+      for (int64_t p = e0 + threadIdx.x; p < e1; p += kFillThreads) {
+        const int c = col[p];
+        const int r = fill_win_row(wrp, nr, p);
+        const uint32_t m = (mask[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
+        if ((m & ((1u << r) - 1u)) == 0u) {  // the column's first row in the window
+          cur[c] += __popc(m);
+          atomicAnd(&mask[c >> 1], ~(0xffffu << ((c & 1) * 16)));
+        }
+      }
+    }
+  }
+}
+
+template <typename VT>
+size_t csc_fill_win_smem(int32_t n_cols) {
+  return (((size_t)n_cols * sizeof(int32_t) + (size_t)((n_cols + 1) / 2) * sizeof(uint32_t) + 15) & ~(size_t)15) +
+         (kFillRows + 1) * sizeof(int64_t);
+}
+
 // Window length W (a multiple of kFillAlign, at most 8192) from the shared
 // memory left after the row-pointer chunk and, when they fit with W >= 1024,
 // the block's cursors.
 template <typename VT>
 static void fill_inst(const Geometry& g, const int64_t* rp, const int32_t* col, const void* Dv, const void* Lv,
                       const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor, int32_t* row_out,
-                      void* DT, void* LT, int* err, cudaStream_t s) {
+                      void* DT, void* LT, int* err, void* rec, int64_t n_out, cudaStream_t s) {
   const size_t limit = g.smem_limit;
+  if (FO_FILL_WIN && csc_fill_win_smem<VT>(n_cols) <= limit) {
+    using R = typename FillRec<VT>::T;
+    const size_t smem = csc_fill_win_smem<VT>(n_cols);
+    cudaFuncSetAttribute(k_csc_fill_win<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_csc_fill_win<VT><<<n_blk, kFillThreads, smem, s>>>(rp, col, (const VT*)Dv, (const VT*)Lv, blk_row, n_cols,
+                                                          cursor, row_out, (VT*)DT, (VT*)LT, (R*)rec);
+    if (rec && n_out > 0)
+      k_csc_split<VT><<<(unsigned)((n_out + 255) / 256), 256, 0, s>>>((const R*)rec, n_out, row_out, (VT*)DT,
+                                                                       (VT*)LT);
+    return;
+  }
   const size_t per_w = 2 * (sizeof(int32_t) + 2 * sizeof(VT));
   auto w_for = [&](bool sc) -> int {
     const size_t fixed = csc_fill_smem<VT>(0, n_cols, sc);
@@ -1897,13 +2089,19 @@ static void fill_inst(const Geometry& g, const int64_t* rp, const int32_t* col, 
   }
 }
 
+size_t csc_fill_rec_bytes(const Geometry& g, int fmt, int32_t n_cols) {
+  if (!FO_FILL_WIN || !FO_FILL_REC) return 0;
+  if (fmt == 0) return csc_fill_win_smem<float>(n_cols) <= g.smem_limit ? sizeof(int4) : 0;
+  return csc_fill_win_smem<uint16_t>(n_cols) <= g.smem_limit ? sizeof(uint2) : 0;
+}
+
 void launch_csc_fill(const Geometry& g, int fmt, const int64_t* rp, const int32_t* col, const void* Dv,
                      const void* Lv, const int64_t* blk_row, int n_blk, int32_t n_cols, int32_t* cursor,
-                     int32_t* row_out, void* DT, void* LT, int* err, cudaStream_t s) {
+                     int32_t* row_out, void* DT, void* LT, int* err, void* rec, int64_t n_out, cudaStream_t s) {
   if (fmt == 0)
-    fill_inst<float>(g, rp, col, Dv, Lv, blk_row, n_blk, n_cols, cursor, row_out, DT, LT, err, s);
+    fill_inst<float>(g, rp, col, Dv, Lv, blk_row, n_blk, n_cols, cursor, row_out, DT, LT, err, rec, n_out, s);
   else
-    fill_inst<uint16_t>(g, rp, col, Dv, Lv, blk_row, n_blk, n_cols, cursor, row_out, DT, LT, err, s);
+    fill_inst<uint16_t>(g, rp, col, Dv, Lv, blk_row, n_blk, n_cols, cursor, row_out, DT, LT, err, rec, n_out, s);
 }
 
 void launch_dequant_csc(int fmt, const int64_t* cp, int32_t n_cols, const int32_t* row, const void* DT,

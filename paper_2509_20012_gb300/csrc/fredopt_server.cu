@@ -242,9 +242,13 @@ int64_t fredopt_footprint_bytes(int64_t n_vox, int32_t n_spots, int64_t nnz, int
   const int fmt = format & 0xff;
   const int64_t vb = fmt == FREDOPT_FP32 ? 4 : 2;
   const int64_t na = ((nnz + 255) & ~255LL) + fo::kPadElems;
-  // peaks of the load: FP32 upload + gathered copy; then, while the 16-bit
-  // index copies are made, CSR + CSC (int32 indices) + both 16-bit copies
-  const int64_t load_peak = std::max(2 * na * 12, na * (2 * (4 + 2 * vb) + 4));
+  // peaks of the load: FP32 upload + gathered copy; the CSC fill's CSR + CSC
+  // + one scratch record per entry (16 bytes with FP32 values, 8 with 16-bit);
+  // while the 16-bit index copies are made, CSR + CSC (int32 indices) + both
+  // 16-bit copies
+  const int64_t rec = vb == 4 ? 16 : 8;
+  const int64_t load_peak =
+      std::max(std::max(2 * na * 12, na * (2 * (4 + 2 * vb) + 4)), na * (2 * (4 + 2 * vb) + rec));
   // resident: CSR with 16-bit columns and CSC with int32 and based 16-bit
   // rows (as much as two int32 copies), the 16-bit copies' FP32 staging, the
   // block headers of the based rows, and their overflow table for wide blocks
