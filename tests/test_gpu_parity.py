@@ -96,8 +96,10 @@ def _csc_of_device_rows(rp, col, D, L, n_cols):
 @pytest.mark.parametrize("fmt", ["fp32", "bf16"])
 def test_csc_bit_exact_shapes(lib, case, fmt):
     """Shapes that take the transpose's other paths: column tables too large
-    for shared memory, rows longer than two bulk-copy windows, and blocks
-    with more rows than one staged row-pointer chunk."""
+    for shared memory (the row-by-row fill with bulk-copy windows), 16-row
+    steps with more entries than the registers hold (the loop form of the
+    row-step fill), and blocks with more rows than one staged row-pointer
+    chunk."""
     rng = np.random.default_rng(17)
     if case == "wide":
         rp, col, D, L = phantom.random_csr(300, 60000, 0.02, seed=1, empty_rows=20)
