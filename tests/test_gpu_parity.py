@@ -427,6 +427,27 @@ def test_checkpoint_resume_bit_exact(lib, tiny):
     np.testing.assert_array_equal(w_res, w_full)
 
 
+def test_trial_steps_past_the_step_table(lib, tiny):
+    """The trial loop takes beta0 alpha^s from a table for s < 65536 and from
+    the FP64 expression beyond: a solve resumed at s = 65526 crosses the end
+    of the table and keeps the oracle's trial counters, decisions and w
+    (Fig. 3; alpha = 0.9999 keeps the steps large enough to matter)."""
+    pl, P, R = tiny
+    alpha, s0, iters = 0.9999, 65536 - 10, 25
+    beta0 = 0.1 * float(np.linalg.norm(pl.w0.astype(np.float64)))
+    with handle(lib, pl) as h:
+        h.begin(pl.w0, alpha, pl.relaxation, beta0=beta0)
+        h.set_state(pl.w0, 0, s0)
+        h.iterate(iters)
+        w, *_ = h.end()
+        log = h.get_log()
+    w_ref, log_ref = oracle.superiorize(P, pl.w0, iters, alpha, pl.relaxation, beta0=beta0, rows=R, s0=s0)
+    assert [e["s"] for e in log] == [e["s"] for e in log_ref]
+    assert [e["accepted"] for e in log] == [e["accepted"] for e in log_ref]
+    assert log[0]["s"] < 65536 < log[-1]["s"]
+    assert np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref) <= 1e-4
+
+
 def test_device_pointers(lib, tiny):
     torch = pytest.importorskip("torch")
     pl, P, R = tiny
