@@ -16,11 +16,12 @@
 //                    float atomics, deterministic).
 //   K3b k_colfinish  per spot: sum of its chunks in order, then the
 //                    gradient, or the clip w <- max(0, x + u) (Fig. 2, last
-//                    loop); advances the iteration counter.
-//   K4 k_finish      one block: deterministic reduction of the partials and
-//                    the closed-form non-ascent trial loop (Fig. 3).
+//                    loop); closes the iteration (log entry, k).
+//   K4 k_finish      64 blocks, then the last one: deterministic two-level
+//                    reduction of the partials and the closed-form
+//                    non-ascent trial loop (Fig. 3) in one warp.
 //   K5 setup         validation, row gather, quantisation, FP64 moments,
-//                    blocked stable counting transpose (CSR -> CSC).
+//                    blocked stable transpose (CSR -> CSC) 16 rows a step.
 #include "fredopt.h"
 #include "fredopt_internal.cuh"
 
