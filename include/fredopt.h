@@ -68,6 +68,15 @@ extern "C" {
  * per nonzero and pass with identical results.  FREDOPT_INDEX32 keeps both
  * streams 32-bit. */
 #define FREDOPT_INDEX32 0x200
+/* launch shapes (or'ed into `format`).  By default every kernel of the plan
+ * is sized for the whole GPU.  FREDOPT_SHARED sizes them for running beside
+ * other plans (a batch graph, a server with several plans in flight): about
+ * one SM's worth of CTAs per 200000 nonzeros of the streamed rows (the whole
+ * GPU from 3.04e7 nonzeros on GB300), so that small plans leave SMs to the
+ * others.  Results depend only on the plan and its launch shapes: a plan
+ * loaded with and without the flag agrees to rounding, and bit for bit with
+ * itself alone and in a batch. */
+#define FREDOPT_SHARED 0x400
 
 /* ---- constraint kinds (Fig. 2 half-spaces; the LETd limit LETd <= Lambda as the half-space (L - Lambda D) w <= 0) ----
  * DOSE_MAX / DOSE_MIN : (D w)_i <= / >= bound                        (Gy)
@@ -411,6 +420,8 @@ int fredopt_get_tuning(fredopt_t h, int64_t* row_cost, int64_t* chunk_cost);
  * streams, one device, timing off) as one CUDA graph per iteration whose
  * branches are the plans, so plans of uneven sizes run concurrently from a
  * single launch.  Each plan's results are bit-identical to running it alone.
+ * Plans loaded with FREDOPT_SHARED leave SMs to each other (small plans use
+ * few CTAs), which raises the batch's throughput.
  * Create after fredopt_begin on every handle (preferably with use_graphs = 0);
  * then fredopt_batch_iterate (asynchronous), fredopt_batch_sync (waits and
  * returns the device time of the iterate calls), fredopt_end per handle. */
@@ -448,10 +459,13 @@ int fredopt_superiorize_batch(const fredopt_t* handles, int n, const float* cons
  * with no request waiting gets a CUDA stream priority below the plans
  * already in flight (an older plan's kernels are scheduled first, younger
  * plans fill the SMs it leaves idle), so it runs about as fast as alone;
- * plans admitted from a backlog share the lowest priority and interleave.  A plan's results do not
- * depend on its co-tenants (tiles depend on the plan alone and a tile's sums
- * on nothing else): they are bit-identical to a fredopt_superiorize call on
- * the same inputs.
+ * plans admitted from a backlog share the lowest priority and interleave.
+ * With max_active > 1 the server loads every plan with FREDOPT_SHARED (launch
+ * shapes for running beside other plans).  A plan's results do not depend on
+ * its co-tenants (tiles depend on the plan and its launch shapes alone and a
+ * tile's sums on nothing else): they are bit-identical to a
+ * fredopt_superiorize call on the same inputs loaded with the same format
+ * (FREDOPT_SHARED added when max_active > 1).
  * All request pointers are host pointers owned by the caller and must stay
  * valid until the request is done (status DONE or an error).  Thread-safe. */
 typedef struct fredopt_request {

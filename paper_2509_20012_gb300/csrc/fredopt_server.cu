@@ -134,7 +134,7 @@ void loader_main(fredopt_server* s) {
     if (rc == FREDOPT_OK) rc = fredopt_create(&h, s->device, q->stream);
     if (rc == FREDOPT_OK)
       rc = fredopt_load_influence(h, r.n_vox, r.n_spots, r.nnz, r.row_ptr, r.col, r.D_val, r.L_val,
-                                  r.voxel_mask, r.format, 0);
+                                  r.voxel_mask, r.format | (s->max_active > 1 ? FREDOPT_SHARED : 0u), 0);
     if (rc == FREDOPT_OK) rc = fredopt_set_constraints(h, (int)q->con.size(), q->con.data());
     if (rc == FREDOPT_OK) rc = fredopt_set_objective(h, (int)q->obj.size(), q->obj.data());
     if (rc == FREDOPT_OK) rc = fredopt_begin(h, r.w0, r.alpha, r.relaxation, &r.params, 0);

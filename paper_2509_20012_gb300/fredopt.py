@@ -22,6 +22,7 @@ DEVICE_PTR = 0x1
 FORMATS = {"fp32": 0, "bf16": 1, "fp16": 2}
 ROWS = {"all": 0x000, "roi": 0x100}
 INDEX32 = 0x200  # keep 32-bit indices in the forward and transposed streams
+SHARED = 0x400   # launch shapes for running beside other plans (batches, servers)
 KINDS = {"DOSE_MIN": 0, "DOSE_MAX": 1, "CDL_MIN": 2, "CDL_MAX": 3, "LETD_MIN": 4, "LETD_MAX": 5}
 QUANTITIES = {"DOSE": 0, "CDL": 1, "LETD": 2}  # LETD: volume statistics only
 VOLUME_MAX_REQUESTS, VOLUME_MAX_BINS, VOLUME_MAX_FRACS = 64, 16384, 64
@@ -288,7 +289,8 @@ class Handle:
         return rc
 
     # ---------------------------------------------------------- plan
-    def load_influence(self, row_ptr, col, D, L, mask, n_spots, fmt="fp32", rows="all", index32=False):
+    def load_influence(self, row_ptr, col, D, L, mask, n_spots, fmt="fp32", rows="all", index32=False,
+                       shared=False):
         dev = _on_device(row_ptr)
         n_vox = int(row_ptr.shape[0]) - 1
         nnz = int(col.shape[0])
@@ -297,7 +299,7 @@ class Handle:
         p_d, k3 = _ptr(D, np.float32)
         p_l, k4 = _ptr(L, np.float32)
         p_m, k5 = _ptr(mask, np.uint32)
-        code = FORMATS[fmt] | ROWS[rows] | (INDEX32 if index32 else 0)
+        code = FORMATS[fmt] | ROWS[rows] | (INDEX32 if index32 else 0) | (SHARED if shared else 0)
         self._check(self.lib.fredopt_load_influence(self.h, n_vox, int(n_spots), nnz, p_rp, p_c, p_d, p_l,
                                                     p_m, code, DEVICE_PTR if dev else 0))
         self.n_vox, self.n_spots = n_vox, int(n_spots)
@@ -315,10 +317,10 @@ class Handle:
                                    float(t["weight"]))
         self._check(self.lib.fredopt_set_objective(self.h, len(terms), arr))
 
-    def load_plan(self, plan, fmt="fp32", rows="all", index32=False):
+    def load_plan(self, plan, fmt="fp32", rows="all", index32=False, shared=False):
         """Load a phantom.Plan-like object (row_ptr, col, D, L, mask, constraints, objective)."""
         self.load_influence(plan.row_ptr, plan.col, plan.D, plan.L, plan.mask, plan.n_spots, fmt=fmt, rows=rows,
-                            index32=index32)
+                            index32=index32, shared=shared)
         self.set_constraints(plan.constraints)
         self.set_objective(plan.objective)
 

@@ -18,9 +18,9 @@ def lib():
     return fredopt
 
 
-def alone(lib, plan, fmt, iters):
+def alone(lib, plan, fmt, iters, shared=False):
     with lib.Handle(0) as h:
-        h.load_plan(plan, fmt=fmt)
+        h.load_plan(plan, fmt=fmt, shared=shared)
         return h.superiorize(plan.w0, iters, 0.99, 1.0)
 
 
@@ -46,15 +46,19 @@ def test_autotune_changes_speed_not_results(lib):
     np.testing.assert_array_equal(w2, ref[0])
 
 
-def test_batch_matches_each_plan_alone(lib):
+@pytest.mark.parametrize("shared", [False, True])
+def test_batch_matches_each_plan_alone(lib, shared):
+    """With whole-GPU launch shapes and with FREDOPT_SHARED ones (small plans
+    on few SMs' worth of CTAs), compared with each plan alone loaded the same
+    way."""
     specs = [(phantom.tiny_plan(), "fp32"), (small_plan(3000, 257, 0.2, 31, 0), "bf16"),
              (small_plan(20000, 1500, 0.05, 32, 0), "fp32"), (phantom.tiny_plan(seed=5), "fp16")]
     iters = 17
-    refs = [alone(lib, p, f, iters) for p, f in specs]
+    refs = [alone(lib, p, f, iters, shared) for p, f in specs]
     hs = []
     for p, f in specs:
         h = lib.Handle(0)
-        h.load_plan(p, fmt=f)
+        h.load_plan(p, fmt=f, shared=shared)
         hs.append(h)
     outs = lib.superiorize_batch(hs, [p.w0 for p, _ in specs], iters, 0.99, 1.0, use_graphs=0)
     for (w, d, l, rep), (wr, dr, lr, rr) in zip(outs, refs):

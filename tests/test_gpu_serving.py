@@ -30,9 +30,11 @@ def small_plan(n_rows, n_cols, density, seed, iters):
                         w0=np.ones(n_cols, np.float32), iters=iters, alpha=0.95, relaxation=1.0)
 
 
-def alone(lib, plan, fmt):
+def alone(lib, plan, fmt, shared=True):
+    """The plan alone, loaded as a server with several plans in flight loads
+    it (FREDOPT_SHARED launch shapes)."""
     with lib.Handle(0) as h:
-        h.load_plan(plan, fmt=fmt)
+        h.load_plan(plan, fmt=fmt, shared=shared)
         return h.superiorize(plan.w0, plan.iters, plan.alpha, plan.relaxation)
 
 
