@@ -138,6 +138,20 @@ def test_16bit_trajectory_vs_oracle(lib, fmt):
         assert rep["objective"] == pytest.approx(oracle.objective(P, w.astype(np.float64)), rel=1e-9)
 
 
+@pytest.mark.parametrize("fmt", ["fp32", "bf16"])
+def test_shared_launch_shapes_trajectory_vs_oracle(lib, fmt):
+    """FREDOPT_SHARED launch shapes (the tiny plan then runs on about ten SMs'
+    worth of CTAs, with other tiles and chunk partials): 100 iterations keep
+    the oracle's trial counters and decisions, w, dose and violations."""
+    plan = phantom.tiny_plan()
+    P, R, w_ref, log_ref = oracle_run(lib, plan, fmt, 100)
+    with lib.Handle(0) as h:
+        h.load_plan(plan, fmt=fmt, shared=True)
+        w, dose, letd, rep = h.superiorize(plan.w0, 100, plan.alpha, plan.relaxation)
+        log = h.get_log()
+    assert_matches_oracle(plan, P, w_ref, log_ref, w, dose, log)
+
+
 def _mixed_plans():
     from test_gpu_serving import small_plan
     return [(phantom.tiny_plan(), "fp32"), (phantom.tiny_plan(seed=3), "bf16"),
