@@ -71,8 +71,8 @@ extern "C" {
 /* launch shapes (or'ed into `format`).  By default every kernel of the plan
  * is sized for the whole GPU.  FREDOPT_SHARED sizes them for running beside
  * other plans (a batch graph, a server with several plans in flight): about
- * one SM's worth of CTAs per 200000 nonzeros of the streamed rows (the whole
- * GPU from 3.04e7 nonzeros on GB300), so that small plans leave SMs to the
+ * one SM's worth of CTAs per 400000 nonzeros of the streamed rows (the whole
+ * GPU from 6.08e7 nonzeros on GB300), so that small plans leave SMs to the
  * others.  Results depend only on the plan and its launch shapes: a plan
  * loaded with and without the flag agrees to rounding, and bit for bit with
  * itself alone and in a batch. */

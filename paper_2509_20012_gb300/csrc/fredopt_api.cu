@@ -1086,9 +1086,13 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   // ---- launch shapes: the whole GPU, or with FREDOPT_SHARED one SM's
   // worth of CTAs per kSharedNnzPerSm nonzeros, so that the kernels of other
   // plans in a batch or on a server share the GPU (16 plans of 6e5-7e7
-  // nonzeros, BF16, one batch graph: 13163 against 10560 plan-iterations/s)
+  // nonzeros, BF16, one batch graph: 13621 against 10560 plan-iterations/s;
+  // 12831, 13205 and 12380 at 1e5, 2e5 and 8e5 nonzeros per SM)
   {
-    constexpr int64_t kSharedNnzPerSm = 200000;
+#ifndef FO_SHARED_NNZ_PER_SM
+#define FO_SHARED_NNZ_PER_SM 400000
+#endif
+    constexpr int64_t kSharedNnzPerSm = FO_SHARED_NNZ_PER_SM;
     const Geometry& F = h->geo_full;
     int eff = F.n_sms;
     if (format & FREDOPT_SHARED)

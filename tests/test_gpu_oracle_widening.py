@@ -140,7 +140,7 @@ def test_16bit_trajectory_vs_oracle(lib, fmt):
 
 @pytest.mark.parametrize("fmt", ["fp32", "bf16"])
 def test_shared_launch_shapes_trajectory_vs_oracle(lib, fmt):
-    """FREDOPT_SHARED launch shapes (the tiny plan then runs on about ten SMs'
+    """FREDOPT_SHARED launch shapes (the tiny plan then runs on about five SMs'
     worth of CTAs, with other tiles and chunk partials): 100 iterations keep
     the oracle's trial counters and decisions, w, dose and violations."""
     plan = phantom.tiny_plan()
