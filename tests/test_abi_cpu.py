@@ -72,6 +72,24 @@ def test_binding_error_constant_matches_header():
     assert 1 << int(re.search(r"#define FREDOPT_WAIT_POLLS \(1 << (\d+)\)", text).group(1)) == fredopt.WAIT_POLLS
     assert int(re.search(r"#define FREDOPT_INDEX32 (0x[0-9a-fA-F]+)", text).group(1), 16) == fredopt.INDEX32
     assert int(re.search(r"#define FREDOPT_ROWS_ROI (0x[0-9a-fA-F]+)", text).group(1), 16) == fredopt.ROWS["roi"]
+    assert int(re.search(r"#define FREDOPT_SHARED (0x[0-9a-fA-F]+)", text).group(1), 16) == fredopt.SHARED
+
+
+def test_footprint_covers_the_load_peak(lib):
+    """The memory estimate the server admits by (a host function: no GPU)
+    covers the load's peak: CSR + CSC + one CSC-build record per nonzero
+    (16 bytes with FP32 values, 8 with 16-bit), at least 40 and 24 bytes per
+    nonzero; it grows with the plan and rejects bad sizes."""
+    fp = lib.fredopt_footprint_bytes
+    nnz = 10_000_000
+    assert fp(1000, 100, nnz, 0) >= 40 * nnz
+    assert fp(1000, 100, nnz, 1) >= 24 * nnz
+    assert fp(1000, 100, nnz, 2) == fp(1000, 100, nnz, 1)
+    assert fp(1000, 100, 2 * nnz, 0) > fp(1000, 100, nnz, 0)
+    assert fp(2_000_000, 100, nnz, 0) > fp(1000, 100, nnz, 0)
+    # the launch-shape and index flags do not change the estimate
+    assert fp(1000, 100, nnz, 0x400) == fp(1000, 100, nnz, 0)
+    assert fp(-1, 100, nnz, 0) == -1 and fp(1000, 0, nnz, 0) == -1 and fp(1000, 100, -1, 0) == -1
 
 
 def test_struct_layouts_match_header(tmp_path):
