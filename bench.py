@@ -8,9 +8,12 @@ superiorized iteration (Fig. 3 around the simultaneous Fig. 2): two fused
 forward products and two transposed products over every voxel row.
 
 Output: one JSON line (rank 0).  `value` is device throughput with the plan
-resident in HBM; `e2e` is one full plan re-optimisation (500 iterations)
-through the public C ABI from pinned host buffers; `roofline` is the dominant
-kernel's algorithmic bytes / its CUDA-event time on the library stream.
+resident in HBM, timed over K graph replays of the iteration (the library's
+path); `e2e` is one full plan re-optimisation (500 iterations) through the
+public C ABI from pinned host buffers; `roofline` is the dominant kernel's
+algorithmic bytes / its CUDA-event time on the library stream, from a second
+timed pass over the same iterations whose graph holds an event pair around
+every kernel (`kernel_timing`).
 Other entries: ROI-row mode, 16-bit storage (both index widths),
 convergence of the violations, the block-iterative sweep, volume statistics,
 continuous-batching serving against sequential FP32, and batching.
