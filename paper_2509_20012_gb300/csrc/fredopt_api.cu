@@ -1111,7 +1111,9 @@ int fredopt_load_influence(fredopt_t h, int64_t n_vox, int32_t n_spots, int64_t 
   // ---- CSC copy of the streamed rows (blocked stable counting transpose)
   {
     // rows without nonzeros (after the others in device order) add nothing
-    const int n_blk = (int)std::max<int64_t>(1, std::min<int64_t>(h->geo.n_sms, n_hot_ne));  // one wave of 1024-thread blocks
+    // one wave of 1024-thread blocks over the whole GPU whatever the plan's
+    // launch shapes (the transpose does not depend on its partition)
+    const int n_blk = (int)std::max<int64_t>(1, std::min<int64_t>(h->geo_full.n_sms, n_hot_ne));
     std::vector<int64_t> blk = partition_rows(rpd, n_hot_ne, n_blk, 1);
     DBuf<int64_t> blk_d, tot_d;
     DBuf<int32_t> cnt;
